@@ -1,0 +1,176 @@
+"""Pins for the oracle's cone-beam projector A and adjoint A^T (CPU only).
+
+The oracle computes A_ij = length of ray i inside voxel j (the linear model of
+Sec. 2.1, Eq. 1, with line-integral rows).  These tests tie it to things other
+than itself: analytic chords through boxes, an independent per-voxel clipping
+written here in numpy, the exact transpose relation, and the discretisation
+limit for a sphere.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import phantoms as P
+
+
+def _brute_dense_A(g):
+    """Dense A by clipping every ray against every voxel box (numpy, slab
+    method), independent of the oracle's incremental walk."""
+    src, pix = P.ray_endpoints(g)
+    S = np.broadcast_to(src[:, None, None, :], pix.shape).reshape(-1, 3)
+    D = pix.reshape(-1, 3) - S
+    n = np.array([g.nx, g.ny, g.nz])
+    vs = np.array([g.vx, g.vy, g.vz])
+    ix, iy, iz = np.meshgrid(np.arange(g.nx), np.arange(g.ny), np.arange(g.nz), indexing="ij")
+    idx = np.stack([ix, iy, iz], -1).reshape(-1, 3)
+    lo = (idx - n / 2.0) * vs
+    hi = lo + vs
+    A = np.zeros((S.shape[0], lo.shape[0]))
+    for r in range(S.shape[0]):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t0 = (lo - S[r]) / D[r]
+            t1 = (hi - S[r]) / D[r]
+        tmin = np.minimum(t0, t1)
+        tmax = np.maximum(t0, t1)
+        par = D[r] == 0
+        if par.any():
+            inside = (S[r] >= lo) & (S[r] <= hi)
+            tmin[:, par] = np.where(inside[:, par], -np.inf, np.inf)
+            tmax[:, par] = np.where(inside[:, par], np.inf, -np.inf)
+        a0 = np.maximum(tmin.max(1), 0.0)
+        a1 = np.minimum(tmax.min(1), 1.0)
+        A[r] = np.maximum(a1 - a0, 0.0) * np.linalg.norm(D[r])
+    return A
+
+
+def _dense_from_oracle(g):
+    M = g.M
+    cols = []
+    for j in range(M):
+        e = np.zeros(M)
+        e[j] = 1.0
+        cols.append(O.forward(g, e.reshape(g.vol_shape())).reshape(-1))
+    return np.stack(cols, 1)
+
+
+@pytest.mark.parametrize("layout", [P.LAYOUT_UV, P.LAYOUT_VU])
+def test_row_sums_are_box_chords(layout):
+    g = P.tiny_geometry(layout=layout)
+    y = O.forward(g, np.ones(g.vol_shape()))
+    ch = P.volume_box_chords(g)
+    assert ch.max() > 5.0
+    np.testing.assert_allclose(y, ch, rtol=0, atol=1e-12)
+
+
+def test_row_sums_are_box_chords_c1_with_misses():
+    g = P.c1_small().geometry
+    y = O.forward(g, np.ones(g.vol_shape()))
+    ch = P.volume_box_chords(g)
+    assert (ch == 0).sum() > 0, "some rays must miss the volume"
+    np.testing.assert_allclose(y, ch, rtol=0, atol=1e-10)
+
+
+def test_voxel_aligned_cube_is_exact():
+    g = P.tiny_geometry(n=(10, 9, 8), vox=(1.0, 1.25, 0.75), det=(16, 14), n_views=7)
+    lo_i = np.array([2, 3, 1])
+    hi_i = np.array([7, 6, 6])
+    x = np.zeros(g.vol_shape())
+    x[lo_i[0]:hi_i[0], lo_i[1]:hi_i[1], lo_i[2]:hi_i[2]] = 0.7
+    n = np.array([g.nx, g.ny, g.nz])
+    vs = np.array([g.vx, g.vy, g.vz])
+    box = P.Box((lo_i - n / 2) * vs, (hi_i - n / 2) * vs, 0.7)
+    exact = P.project_analytic([box], g)
+    assert exact.max() > 1.0
+    np.testing.assert_allclose(O.forward(g, x), exact, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("layout", [P.LAYOUT_UV, P.LAYOUT_VU])
+def test_matches_bruteforce_clipping_8cubed(layout):
+    g = P.tiny_geometry(layout=layout)
+    A_brute = _brute_dense_A(g)
+    A_or = _dense_from_oracle(g)
+    assert np.count_nonzero(A_brute > 1e-9) > 1000
+    np.testing.assert_allclose(A_or, A_brute, rtol=0, atol=1e-12)
+
+
+def test_adjoint_is_dense_transpose():
+    g = P.tiny_geometry(n=(6, 7, 5), det=(9, 8), n_views=5)
+    A = _dense_from_oracle(g)
+    cols = []
+    for r in range(g.N):
+        e = np.zeros(g.N)
+        e[r] = 1.0
+        cols.append(O.adjoint(g, e.reshape(g.proj_shape())).reshape(-1))
+    At = np.stack(cols, 1)
+    np.testing.assert_allclose(At, A.T, rtol=0, atol=1e-13)
+
+
+def test_dot_product_identity_c1():
+    g = P.c1_small().geometry
+    x = P.random_volume(g, 3)
+    y = P.random_projections(g, 4)
+    lhs = float((O.forward(g, x) * y).sum())
+    rhs = float((x * O.adjoint(g, y)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_adjoint_by_voxel_clipping_matches_walk():
+    g = P.tiny_geometry(n=(9, 8, 7), det=(14, 12), n_views=9, arc=200.0)
+    y = P.random_projections(g, 5)
+    full = O.adjoint(g, y).reshape(-1)
+    vox = np.arange(g.M)
+    np.testing.assert_allclose(O.adjoint_voxels(g, y, vox), full, rtol=0, atol=1e-12)
+
+
+def test_forward_rays_subset():
+    g = P.c1_small().geometry
+    x = P.random_volume(g, 8)
+    y = O.forward(g, x).reshape(-1)
+    rays = np.random.default_rng(1).choice(g.N, 500, replace=False)
+    np.testing.assert_array_equal(O.forward_rays(g, x, rays), y[rays])
+
+
+def test_layouts_are_permutations():
+    gu = P.tiny_geometry(layout=P.LAYOUT_UV)
+    gv = P.tiny_geometry(layout=P.LAYOUT_VU)
+    x = P.random_volume(gu, 9)
+    yu = O.forward(gu, x)
+    yv = O.forward(gv, x)
+    np.testing.assert_array_equal(yu, np.transpose(yv, (0, 2, 1)))
+
+
+def test_sphere_discretisation_error_shrinks():
+    """A applied to a voxelised sphere approaches the analytic chord as the
+    voxel size shrinks (first order on rays that do not graze the surface;
+    grazing rays converge only like the square root of the voxel size)."""
+    mean_err, max_err = [], []
+    for n in (16, 32, 64):
+        vox = 32.0 / n
+        g = P.Geometry(n, n, n, vox, vox, vox, 24, 24, 1.6, 1.6, 200.0, 320.0,
+                       P.scan_angles(4, 360.0, 3.0))
+        sph = P.Ellipsoid(np.array([1.3, -0.7, 0.9]), np.full(3, 9.0), np.eye(3), 1.0)
+        x = P.voxelize([sph], g, ss=4)
+        exact = P.project_analytic([sph], g)
+        core = exact > 0.6 * exact.max()
+        e = np.abs(O.forward(g, x) - exact)[core]
+        mean_err.append(e.mean())
+        max_err.append(e.max())
+    assert mean_err[1] < 0.6 * mean_err[0] and mean_err[2] < 0.6 * mean_err[1], mean_err
+    assert max_err[1] < 0.6 * max_err[0] and max_err[2] < 0.6 * max_err[1], max_err
+    assert mean_err[2] < 0.01 * 18.0
+
+
+def test_nnz_count_matches_dense_pattern():
+    g = P.tiny_geometry()
+    A = _brute_dense_A(g)
+    # pieces of positive length; each (ray, voxel) pair is one piece except
+    # where a walk splits a voxel, which cannot happen for convex voxels
+    assert O.count_nnz(g) == int(np.count_nonzero(A > 0))
+
+
+def test_geometry_check_rejects_source_inside():
+    g = P.tiny_geometry()
+    assert O.check(g)
+    assert not O.check(g.replace(dso=4.0))
+    assert not O.check(g.replace(dsd=g.dso + 2.0))
+    assert not O.check(g.replace(nz=0))
