@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the IRN-PICCS reconstruction path on GB300.
+
+One step = one full IRN-PICCS reconstruction (3 reweighting cycles x 10 CGLS
+iterations) of the 256^3 x 1 mm volume from 90 cone-beam views of 512 x 512
+pixels (0.8 mm) over a 200 degree short scan, with every step of the path
+(projector A, matched adjoint A^T, PICCS weights and stencils, Krylov vector
+work) in this repository's CUDA kernels, inputs resident in HBM.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.  Under torchrun every rank
+runs an independent replica on its own GPU (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import phantoms as P  # noqa: E402
+
+METRIC = "PICCS-Krylov recon ms/scan p50 at 256^3 (90 views of 512^2, 30 its)"
+UNIT = "ms/scan"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    scan = P.c2_needle()
+    return scan
+
+
+def workload_config(scan):
+    g = scan.geometry
+    return {
+        "workload": (f"{scan.name}: {g.nx}^3 x {g.vx:g} mm volume, {g.n_views} views over 200 deg, "
+                     f"{g.nu}x{g.nv} detector x {g.du:g} mm, DSO {g.dso:g} / DSD {g.dsd:g} mm, "
+                     f"IRN-PICCS {scan.n_outer} cycles x {scan.n_inner} CGLS iterations"),
+        "volume": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.nu, g.nv],
+        "iterations": scan.iterations, "alpha": scan.alpha, "lambda": scan.lam, "tau": scan.tau,
+        "projection_layout": "view,u,v (v fastest)",
+        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); working set ~0.9 GB",
+        "parallelism": "replicas (one independent reconstruction per GPU)",
+    }
+
+
+def nnz_of(scan):
+    with open(os.path.join(ROOT, "tests", "golden", "nnz_counts.json")) as f:
+        return int(json.load(f)[scan.name]["nnz"])
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_record(kernel):
+    """Per-launch DRAM traffic from a committed ncu summary, valid only while
+    the projector source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "projector_traffic.json")
+    src = os.path.join(ROOT, "paper_2509_08574_gb300", "csrc", "kernels_project.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if rec.get("source_sha256") != h:
+        return None
+    ent = rec.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = ["-i", str(device_index)]
+        self.sel = sel
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *self.sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def pctl(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample(scan, b, xp):
+    """Times the FP64 oracle on a bounded sample of the workload: A and A^T on
+    one view in ten, plus one pass of the regularisation blocks over the full
+    volume; extrapolated to a whole reconstruction."""
+    import oracle as O
+
+    g = scan.geometry
+    sub = list(range(0, g.n_views, 10))
+    gs = g.replace(angles=g.angles[sub])
+    bsub = np.ascontiguousarray(b[sub], dtype=np.float64)
+    x64 = xp.astype(np.float64)
+    t0 = time.perf_counter()
+    O.forward(gs, x64)
+    t1 = time.perf_counter()
+    O.adjoint(gs, bsub)
+    t2 = time.perf_counter()
+    g3 = O.grad(x64)
+    w = O.weights(g3, scan.tau)
+    O.grad_adj(w[None] * g3)
+    O.grad_adj(w[None] * g3)
+    t3 = time.perf_counter()
+    scale = g.n_views / len(sub)
+    pair = scale * ((t1 - t0) + (t2 - t1)) + (t3 - t2)
+    # explicit-residual CGLS: one (A, A^T) pair to restart each cycle plus one
+    # per iteration
+    per_scan_s = scan.n_outer * (scan.n_inner + 1) * pair
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"A and A^T on {len(sub)} of {g.n_views} views plus one regularisation pass on the "
+              f"full {g.nx}^3 volume ({t3 - t0:.1f} s), scaled to {scan.n_outer}x"
+              f"({scan.n_inner}+1) projector pairs per scan")
+    return per_scan_s * 1e3, cores, sample, t3 - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    scan = workload()
+    b = scan.measured()
+    xp = scan.prior_volume(ss=1)
+    for _ in range(args.warmup):
+        oracle_sample(scan, b, xp)
+    vals = []
+    cores = sample = None
+    for _ in range(args.steps):
+        v, cores, sample, _ = oracle_sample(scan, b, xp)
+        vals.append(v)
+    value = pctl(vals, 50)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(scan),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our CUDA path
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2509_08574_gb300 as pk
+
+    scan = workload()
+    g = scan.geometry
+    t_in = time.perf_counter()
+    b_np = scan.measured()
+    xp_np = scan.prior_volume(ss=1)
+    t_in = time.perf_counter() - t_in
+
+    stream = torch.cuda.Stream()
+    b = torch.from_numpy(b_np).cuda()
+    xp = torch.from_numpy(xp_np).cuda()
+    out = torch.empty(g.vol_shape(), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner)
+    torch.cuda.synchronize()
+    ctx = pk.Context(g, stream=stream)
+    ctx.set_prior(xp)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            ctx.reconstruct(b, params, out=out)
+    stream.synchronize()
+    rep = ctx.report()
+    if rep.status != 0 or rep.iterations_run != scan.iterations:
+        raise RuntimeError(f"reconstruction status {rep.status}, {rep.iterations_run} iterations")
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ctx.profile_enable(True)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()  # outside the step's events: L2 holds no input at step start
+            ev[k][0].record(stream)
+            ctx.reconstruct(b, params, out=out)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    p50, p99 = pctl(step_ms, 50), pctl(step_ms, 99)
+    total_ms = float(sum(step_ms))
+
+    if world > 1:
+        t = torch.tensor([p50, p99, total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p50, p99, total_ms = (float(v) for v in t.tolist())
+
+    # end to end through the public API with host buffers (copies inside)
+    hb = torch.from_numpy(b_np).pin_memory()
+    hout = torch.empty(g.vol_shape(), dtype=torch.float32).pin_memory()
+    ctx.set_stream(stream)
+    e2e_ms = []
+    for k in range(args.e2e_steps + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        ctx.reconstruct_host(hb, params, out=hout)
+        dt = (time.perf_counter() - t0) * 1e3
+        if k > 0:  # first call warms the pinned-memory path
+            e2e_ms.append(dt)
+    e2e_p50 = pctl(e2e_ms, 50)
+    if world > 1:
+        t = torch.tensor([e2e_p50], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_p50 = float(t.item())
+
+    # roofline of the dominant kernel (measured live inside the timed region)
+    nnz = nnz_of(scan)
+    peaks, peak_kind = measured_peaks()
+    per = {}
+    for kind in ("forward", "adjoint"):
+        n = prof["launches"][kind]
+        per[kind] = (prof["total_ms"][kind] / n) if n else float("nan")
+    dom = max(("forward", "adjoint"), key=lambda k: prof["total_ms"][k])
+    alg_bytes = 4.0 * (nnz + g.M + g.N)
+    achieved = alg_bytes / (per[dom] * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    kernel_names = {"forward": "fwd_kernel", "adjoint": "adj_kernel"}
+
+    line = {
+        "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(scan),
+        "p50_ms": p50, "p99_ms": p99,
+        "job_scans_per_s": world * args.steps / (total_ms * 1e-3),
+        "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(g.N * 4),
+                "d2h_bytes_per_step": int(g.M * 4)},
+        "gpu_launches": int(prof["total_launches"]),
+        "kernel_ms_per_step": {k: v / args.steps for k, v in prof["total_ms"].items()},
+        "launches_per_step": {k: v / args.steps for k, v in prof["launches"].items()},
+        "projector": {"nnz": nnz, "fwd_ms": per["forward"], "adj_ms": per["adjoint"],
+                      "fwd_gups": nnz / (per["forward"] * 1e-3) / 1e9,
+                      "adj_gups": nnz / (per["adjoint"] * 1e-3) / 1e9},
+        "roofline": {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_record(kernel_names[dom]),
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "clocks": clk,
+        "wall_s_timed_region": t_wall, "input_generation_s": t_in,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = oracle_sample(scan, b_np, xp_np)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * piccs.h -- C ABI of the GB300 (sm_103a) IRN-PICCS cone-beam reconstruction
+ * library (libpiccs.so).
+ *
+ * Method (Hastings, Islam, Sabate Landman et al., "Real-time CBCT
+ * reconstructions using Krylov solvers in repeated scanning procedures"):
+ *   CT is the linear model A x + e = b (Sec. 2.1, Eq. 1).  Given a prior
+ *   reconstruction x_p, PICCS minimises ||Ax-b||^2 + alpha^2 TV(x)
+ *   + lambda^2 TV(x - x_p) (Eq. 3).  The IRN scheme (Sec. 2.2-2.3, Eqs. 6-11)
+ *   replaces each TV term by a weighted 2-norm whose weights
+ *   W(Dz)_ii = (sqrt(sum_d [D_d z]_i^2) + tau^2)^(-1/2) are frozen at the
+ *   previous outer iterate, and solves each reweighted problem approximately
+ *   with a few CGLS iterations on the augmented least-squares system
+ *   [A; alpha W1 D; lambda W2 D] x ~ [b; 0; lambda W2 D x_p] (the display after
+ *   Eq. 11), warm-started at the previous iterate.
+ *
+ * Conventions shared by every call:
+ *   - Geometry: circular cone beam, rotation axis z, volume centred at the
+ *     origin; source S_j = DSO (cos t_j, sin t_j, 0); detector centre
+ *     -(DSD - DSO)(cos t_j, sin t_j, 0); detector axes u = (-sin t_j, cos t_j, 0),
+ *     v = (0, 0, 1); pixel (iu, iv) centre at (iu - (nu-1)/2) du along u and
+ *     (iv - (nv-1)/2) dv along v; one ray per pixel from the source through
+ *     the pixel centre.  The paper names only DSO, DSD and the pitch
+ *     (Sec. 3.2); the rest is this library's convention.
+ *   - A_ij = length in mm of ray i inside voxel j (exact ray/voxel-box
+ *     intersection, i.e. Siddon weights).  A^T uses the same weights.
+ *   - Volume layout: float32, index (ix*ny + iy)*nz + iz (z fastest).
+ *   - Projection layout: PICCS_LAYOUT_UV: (j*nu + iu)*nv + iv (v fastest, the
+ *     native and fastest one); PICCS_LAYOUT_VU: (j*nv + iv)*nu + iu.
+ *   - Pointers named d_* are CUDA device pointers in the current device's
+ *     address space, h_* are host pointers.  The caller owns them; the library
+ *     never frees or keeps them after the call returns (except d_* buffers
+ *     read asynchronously, which must stay valid until the stream work ends).
+ *     Device buffers must be 16-byte aligned (cudaMalloc/torch allocations
+ *     are); misaligned buffers are still accepted but take slower paths.
+ *   - Every call that launches work enqueues it on the context's stream and
+ *     returns without waiting, unless its comment says it synchronises.
+ *   - Return value: PICCS_OK (0) or a negative PICCS_E* code; nothing is
+ *     thrown across the ABI.  piccs_last_error() gives a message.
+ *   - Sizes: M = nx*ny*nz and N = n_views*nu*nv must each be below 2^31.
+ */
+#ifndef PICCS_H
+#define PICCS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PICCS_OK 0
+#define PICCS_EINVAL (-1)      /* invalid argument or geometry */
+#define PICCS_ENOMEM (-2)      /* not enough device memory (checked first) */
+#define PICCS_ENONFINITE (-3)  /* NaN or Inf found in an input */
+#define PICCS_EBREAKDOWN (-4)  /* Krylov breakdown (non-positive or NaN scalar) */
+#define PICCS_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define PICCS_ECUDA (-6)       /* a CUDA runtime call failed */
+#define PICCS_ENOTIMPL (-7)    /* not available in this build */
+
+enum { PICCS_LAYOUT_UV = 0, PICCS_LAYOUT_VU = 1 };
+
+/* Regulariser variants: PICCS (Eq. 3), PIPLE (Eq. 4: lambda^2 ||x - x_p||^2
+ * instead of the prior TV term), TV (lambda ignored), CGLS (alpha and lambda
+ * ignored: plain CGLS on A x ~ b, the paper's unregularised comparison). */
+enum { PICCS_VARIANT_PICCS = 0, PICCS_VARIANT_PIPLE = 1, PICCS_VARIANT_TV = 2,
+       PICCS_VARIANT_CGLS = 3 };
+
+/* Weight rule: R1 is the paper's (|g| + tau^2)^(-1/2); R2 is the common
+ * (|g|^2 + tau^2)^(-1/4). */
+enum { PICCS_WEIGHT_R1 = 0, PICCS_WEIGHT_R2 = 1 };
+
+/* Initial guess: the prior x_p (default), zero, or a caller volume. */
+enum { PICCS_X0_PRIOR = 0, PICCS_X0_ZERO = 1, PICCS_X0_USER = 2 };
+
+typedef struct {
+    int nx, ny, nz;            /* voxels */
+    double vx, vy, vz;         /* voxel size, mm (> 0) */
+    int nu, nv;                /* detector pixels */
+    double du, dv;             /* detector pitch, mm (> 0) */
+    double dso, dsd;           /* source-axis and source-detector distance, mm;
+                                  the source and the detector must lie outside
+                                  the cylinder circumscribing the volume */
+    int n_views;               /* >= 1 */
+    const double *angles_rad;  /* host array of n_views angles; copied */
+    int proj_layout;           /* PICCS_LAYOUT_UV or PICCS_LAYOUT_VU */
+} piccs_geometry;
+
+typedef struct {
+    float alpha, lambda;       /* regularisation parameters (>= 0), Eq. 3 */
+    float tau;                 /* smoothing parameter (> 0), the weight equation */
+    int n_outer;               /* IRN reweighting cycles (>= 1) */
+    int n_inner;               /* CGLS iterations per cycle (>= 0);
+                                  total iterations = n_outer * n_inner */
+    int x0_mode;               /* PICCS_X0_* */
+    int variant;               /* PICCS_VARIANT_* */
+    int weight_rule;           /* PICCS_WEIGHT_* */
+} piccs_params;
+
+/* What the last reconstruction did (filled by piccs_report, which waits). */
+typedef struct {
+    int status;                /* PICCS_OK, PICCS_EBREAKDOWN or PICCS_ENONFINITE */
+    int iterations_run;        /* inner iterations that changed x */
+    int n_history;             /* entries written to gamma_history */
+    double gamma_history[512]; /* ||A~^T r~||^2 at the start of each cycle and
+                                  after every inner iteration, in order */
+} piccs_stats;
+
+/* Kernel accounting of a context (see piccs_profile_enable). */
+enum { PICCS_KERNEL_FORWARD = 0, PICCS_KERNEL_ADJOINT = 1, PICCS_KERNEL_REG = 2,
+       PICCS_KERNEL_VECTOR = 3, PICCS_KERNEL_SCALAR = 4, PICCS_KERNEL_CLASSES = 5 };
+
+typedef struct {
+    long long launches[PICCS_KERNEL_CLASSES]; /* kernels launched per class */
+    double total_ms[PICCS_KERNEL_CLASSES];    /* summed device time per class (only
+                                                 while timing is enabled, else 0) */
+    long long total_launches;                 /* all kernels of this library */
+} piccs_profile;
+
+typedef struct piccs_ctx piccs_ctx;
+
+/* Create a context for one scanner geometry: validates it, copies it,
+ * checks device memory for the reconstruction workspace (PICCS_ENOMEM before
+ * any allocation), allocates the workspace on the current device and
+ * uploads the per-view ray tables.  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  Synchronises.  Paper: Sec. 3 (one geometry per
+ * scanning procedure, repeated scans of the same patient). */
+int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_stream);
+
+/* Free the context and its device memory (synchronises its stream). */
+void piccs_destroy(piccs_ctx *ctx);
+
+/* Message for the last failing call on ctx (or of piccs_create when ctx is
+ * NULL, per thread).  Valid until the next call on the same context. */
+const char *piccs_last_error(const piccs_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+int piccs_set_stream(piccs_ctx *ctx, void *cuda_stream);
+
+/* Device bytes piccs_create allocates for this geometry (params may be NULL).
+ * Pure host computation; needs no GPU. */
+int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
+                          size_t *bytes);
+
+/* Check a geometry and parameters without creating anything (params may be
+ * NULL).  Pure host computation; needs no GPU. */
+int piccs_validate(const piccs_geometry *geometry, const piccs_params *params);
+
+/* Copy the prior reconstruction x_p (M floats, device) into context-owned
+ * memory and check it for NaN/Inf (PICCS_ENONFINITE).  Synchronises.
+ * Paper: x_p, the "good initial reconstruction" of Sec. 2.1 and Sec. 3. */
+int piccs_set_prior(piccs_ctx *ctx, const float *d_xprior);
+
+/* IRN-PICCS reconstruction (Sec. 2.3): writes M floats to d_vol_out.
+ * d_proj: N measured log projections b in the context layout.  d_x0: initial
+ * volume when params->x0_mode == PICCS_X0_USER, else ignored (may be NULL).
+ * The prior must have been set unless variant is TV or CGLS with x0 != PRIOR.
+ * Asynchronous: the Krylov scalars stay on the device; breakdown or a NaN/Inf
+ * in d_proj is reported by piccs_report. */
+int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *params,
+                      const float *d_x0, float *d_vol_out);
+
+/* Same with host buffers: copies h_proj (and h_x0) to the device, runs
+ * piccs_reconstruct and copies the volume back to h_vol_out.  Synchronises;
+ * returns the device status (PICCS_EBREAKDOWN, PICCS_ENONFINITE) too. */
+int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_params *params,
+                           const float *h_x0, float *h_vol_out);
+
+/* Wait for the context's stream and describe the last reconstruction. */
+int piccs_report(piccs_ctx *ctx, piccs_stats *out);
+
+/* Forward projection d_proj = A d_vol (Eq. 1): N floats from M floats. */
+int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj);
+
+/* Matched backprojection d_vol = A^T d_proj (same ray/voxel weights as
+ * piccs_forward): M floats from N floats.  Needed by every Krylov step
+ * (Sec. 2.3, the text after the augmented system). */
+int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol);
+
+/* The reweighting step of one IRN cycle (Eqs. 10-11): from the current
+ * iterate d_x and the prior, writes per voxel
+ *   d_omega = alpha^2 w1^2 + lambda^2 w2^2      (PICCS; alpha^2 w1^2 otherwise)
+ *   d_c     = lambda^2 D^T W2^2 D x_p           (PICCS; lambda^2 x_p for PIPLE;
+ *                                                0 for TV and CGLS)
+ * with w1 = W(D x), w2 = W(D x - D x_p).  M floats each. */
+int piccs_reg_weights(piccs_ctx *ctx, const float *d_x, const piccs_params *params,
+                      float *d_omega, float *d_c);
+
+/* Regularisation block of the normal operator of the augmented system:
+ *   d_out = D^T diag(omega) D d_z   (+ lambda^2 d_z for PIPLE)
+ * and *h_rho = sum_i omega_i |(D z)_i|^2 (+ lambda^2 |z|^2 for PIPLE), i.e.
+ * ||[alpha W1 D; lambda W2 D] z||^2.  M floats.  Synchronises (h_rho may be
+ * NULL, then it does not). */
+int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *params,
+                     const float *d_z, float *d_out, double *h_rho);
+
+/* Reset the context's kernel accounting and switch per-launch device timing
+ * on (timing != 0) or off.  With timing on, every kernel launch is bracketed
+ * by two CUDA events on the context's stream; launches are always counted. */
+int piccs_profile_enable(piccs_ctx *ctx, int timing);
+
+/* Wait for the context's stream and read the accounting since the last
+ * piccs_profile_enable.  Synchronises. */
+int piccs_profile_read(piccs_ctx *ctx, piccs_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICCS_H */

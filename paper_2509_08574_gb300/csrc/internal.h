@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of libpiccs.
+// Nothing here is part of the public C ABI (include/piccs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace piccs {
+
+// Per (view, detector column) ray-walk constants, computed in FP64 on the host
+// and rounded once.  All rays of one detector column share their projection
+// onto the xy plane (the detector v axis is parallel to the rotation axis and
+// the source lies in z = 0), so the xy part of the Siddon walk is identical
+// for the whole column; only the z crossings depend on the row.
+//
+// The xy walk is parametrised by s = xy distance (mm) from the point where the
+// column's rays enter the volume's xy square:
+//   x plane k (voxel units, 0..nx) is crossed at s = (k - ex) * inv_dx,
+//   y plane k                        at s = (k - ey) * inv_dy,
+//   the square is left at s = L.
+// (ex, ey) is the entry point in voxel units and (ix0, iy0) = floor of it,
+// so the first crossing ahead is never behind s = 0.  A direction parallel to
+// the x planes has inv_dx = +inf and ex = -1e30 (every crossing at +inf).
+// Row v (detector height, mm) has z (voxel units, centred) = v * kE + s / (KD / v)
+// and 3D length per unit s of sqrt(1 + (v * invD)^2).
+struct __align__(16) ColParams {
+    float inv_dx, ex, inv_dy, ey;
+    float L, kE, KD, invD;
+    int ix0, iy0, stepx, stepy;
+    int pad0, pad1, pad2, pad3;
+};
+
+struct ProjGeom {
+    int nx, ny, nz;
+    int nu, nv, n_views;
+    long long sj, su, sv;   // projection strides of view, column, row
+    float halfnz;           // nz / 2
+};
+
+// Device-side Krylov scalars (FP64), read by every vector kernel so that no
+// value has to come back to the host between kernels.
+struct KrylovScalars {
+    double gamma;     // ||s||^2 of the current normal-equations residual s = A~^T r~
+    double gamma0;    // gamma at the start of the current cycle
+    double delta;     // ||A~ p||^2
+    double a;         // step length gamma / delta (0 when stopped or broken down)
+    double beta;      // gamma_new / gamma_old (0 right after a restart)
+    int status;       // 0, or a negative PICCS_E* code
+    int iters_run;    // inner iterations with a != 0
+    int n_hist;
+    int stopped;      // the cycle converged (gamma <= 1e-26 gamma0)
+    int nonfinite;    // a NaN/Inf was seen in an input
+    int pad;
+    double hist[512];
+};
+
+enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1 };
+
+// ---- projector (kernels_project.cu) ----
+int project_blocks(const ProjGeom &g);
+cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float *vrow,
+                           const float *vol, float *out, int mode, const float *b,
+                           double *partials, int *nonfinite, cudaStream_t st);
+// vol += A^T proj (vol must hold the starting values, e.g. zeros)
+cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float *vrow,
+                           const float *proj, float *vol, cudaStream_t st);
+
+// ---- regulariser (kernels_reg.cu) ----
+struct VolDims { int nx, ny, nz; };
+int stencil_blocks(long long M);
+cudaError_t launch_weights(VolDims d, const float *x, const float *xp, float alpha2,
+                           float lambda2, float tau2, int rule, int variant, float *omega,
+                           float *w2sq, cudaStream_t st);
+cudaError_t launch_prior_rhs(VolDims d, const float *xp, const float *w2sq, float lambda2,
+                             int variant, float *c, cudaStream_t st);
+// out = D^T diag(omega) D z (+ lam2_piple z); partials (may be null) get
+// sum omega |Dz|^2 (+ lam2_piple z^2) per block.
+cudaError_t launch_reg_normal(VolDims d, const float *z, const float *omega, float lam2_piple,
+                              float *out, double *partials, cudaStream_t st);
+// Restart of a Krylov cycle: gn = c - D^T Omega D x (- lam2_piple x);
+// first: g = gn, s = gn; else s += gn - g, g = gn, partials get s^2.
+cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, float lam2_piple,
+                               const float *c, float *g, float *s, int first, double *partials,
+                               cudaStream_t st);
+
+// ---- Krylov vector work (kernels_krylov.cu) ----
+int vector_blocks();
+cudaError_t launch_p_update(long long M, const float *s, float *p, const KrylovScalars *k,
+                            cudaStream_t st);
+cudaError_t launch_x_update(long long M, long long N, float *x, const float *p, float *g,
+                            const float *t, float *s, float *r, const float *q,
+                            const KrylovScalars *k, cudaStream_t st);
+cudaError_t launch_norm2(long long n, const float *v, double *partials, cudaStream_t st);
+cudaError_t launch_finalize_delta(KrylovScalars *k, const double *pa, int na, const double *pb,
+                                  int nb, cudaStream_t st);
+cudaError_t launch_finalize_gamma(KrylovScalars *k, const double *p, int n, int restart,
+                                  cudaStream_t st);
+cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st);
+cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st);
+cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st);
+
+}  // namespace piccs

@@ -1,0 +1,229 @@
+// PICCS regularisation terms for sm_103a: IRN weights, the prior right-hand
+// side and the regularisation block of the normal operator.
+//
+// D stacks the forward differences (D_d z)_i = z_i - z_{i+e_d} along x, y, z
+// (D1 rows [1, -1], Sec. 2.2), each zero where i+e_d leaves the grid.  With
+// the weights frozen per IRN cycle (Eqs. 10-11), the two regularisation blocks
+// alpha W1 D and lambda W2 D of the augmented system enter the normal
+// equations only through one combined per-voxel field
+//   omega = alpha^2 w1^2 + lambda^2 w2^2,
+// because W1 and W2 repeat the same value over the three directions:
+//   [alpha W1 D; lambda W2 D]^T [alpha W1 D; lambda W2 D] = D^T diag(omega) D,
+// and the right-hand side block is c = lambda^2 D^T W2^2 D x_p.  So the solver
+// never stores the 6M augmented rows; each application is one 7-point stencil
+// pass.  All kernels are memory-bound streaming passes over z-fastest volumes:
+// consecutive threads take consecutive z, the +-1 and +-nz neighbours come
+// from L1 and the +-ny*nz neighbours from L2.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace piccs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void unflatten(long long i, int ny, int nz, int &ix, int &iy, int &iz)
+{
+    iz = (int)(i % nz);
+    const long long t = i / nz;
+    iy = (int)(t % ny);
+    ix = (int)(t / ny);
+}
+
+// w^2 for a gradient with squared Euclidean norm n2 (tau2 = tau^2):
+// R1 1/(|g| + tau^2), R2 1/sqrt(|g|^2 + tau^2)
+__device__ __forceinline__ float weight_sq(float n2, float tau2, int rule)
+{
+    if (rule == 0) return 1.f / (sqrtf(n2) + tau2);
+    return rsqrtf(n2 + tau2);
+}
+
+__global__ void __launch_bounds__(kThreads)
+weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float *__restrict__ xp,
+               float alpha2, float lambda2, float tau2, int rule, int variant,
+               float *__restrict__ omega, float *__restrict__ w2sq)
+{
+    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        unflatten(i, d.ny, d.nz, ix, iy, iz);
+        const float xi = x[i];
+        const float gx = (ix + 1 < d.nx) ? xi - x[i + sx] : 0.f;
+        const float gy = (iy + 1 < d.ny) ? xi - x[i + sy] : 0.f;
+        const float gz = (iz + 1 < d.nz) ? xi - x[i + 1] : 0.f;
+        float om = 0.f;
+        if (variant != 3) om = alpha2 * weight_sq(gx * gx + gy * gy + gz * gz, tau2, rule);
+        if (variant == 0) {
+            const float di = xi - xp[i];
+            const float hx = (ix + 1 < d.nx) ? di - (x[i + sx] - xp[i + sx]) : 0.f;
+            const float hy = (iy + 1 < d.ny) ? di - (x[i + sy] - xp[i + sy]) : 0.f;
+            const float hz = (iz + 1 < d.nz) ? di - (x[i + 1] - xp[i + 1]) : 0.f;
+            const float w2 = weight_sq(hx * hx + hy * hy + hz * hz, tau2, rule);
+            om += lambda2 * w2;
+            w2sq[i] = w2;
+        }
+        omega[i] = om;
+    }
+}
+
+// c = lambda^2 D^T W2^2 D x_p (PICCS), lambda^2 x_p (PIPLE), 0 otherwise
+__global__ void __launch_bounds__(kThreads)
+prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
+                 const float *__restrict__ w2sq, float lambda2, int variant, float *__restrict__ c)
+{
+    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        float out = 0.f;
+        if (variant == 0) {
+            int ix, iy, iz;
+            unflatten(i, d.ny, d.nz, ix, iy, iz);
+            const float pi = xp[i], wi = w2sq[i];
+            float acc = 0.f;
+            if (ix + 1 < d.nx) acc += wi * (pi - xp[i + sx]);
+            if (iy + 1 < d.ny) acc += wi * (pi - xp[i + sy]);
+            if (iz + 1 < d.nz) acc += wi * (pi - xp[i + 1]);
+            if (ix >= 1) acc -= w2sq[i - sx] * (xp[i - sx] - pi);
+            if (iy >= 1) acc -= w2sq[i - sy] * (xp[i - sy] - pi);
+            if (iz >= 1) acc -= w2sq[i - 1] * (xp[i - 1] - pi);
+            out = lambda2 * acc;
+        } else if (variant == 1) {
+            out = lambda2 * xp[i];
+        }
+        c[i] = out;
+    }
+}
+
+// t = D^T diag(omega) D z (+ lam2 z) at voxel i, and omega |(Dz)_i|^2 (+ lam2 z_i^2)
+__device__ __forceinline__ float stencil_at(VolDims d, long long i, const float *__restrict__ z,
+                                            const float *__restrict__ omega, float lam2,
+                                            float &energy)
+{
+    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    int ix, iy, iz;
+    unflatten(i, d.ny, d.nz, ix, iy, iz);
+    const float zi = z[i];
+    const float w = omega[i];
+    const float gx = (ix + 1 < d.nx) ? zi - z[i + sx] : 0.f;
+    const float gy = (iy + 1 < d.ny) ? zi - z[i + sy] : 0.f;
+    const float gz = (iz + 1 < d.nz) ? zi - z[i + 1] : 0.f;
+    float t = w * (gx + gy + gz);
+    if (ix >= 1) t -= omega[i - sx] * (z[i - sx] - zi);
+    if (iy >= 1) t -= omega[i - sy] * (z[i - sy] - zi);
+    if (iz >= 1) t -= omega[i - 1] * (z[i - 1] - zi);
+    t = fmaf(lam2, zi, t);
+    energy = w * (gx * gx + gy * gy + gz * gz) + lam2 * zi * zi;
+    return t;
+}
+
+__device__ __forceinline__ void block_sum_store(double v, double *partials)
+{
+    __shared__ double red[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+template <bool NORM>
+__global__ void __launch_bounds__(kThreads)
+reg_normal_kernel(VolDims d, long long M, const float *__restrict__ z,
+                  const float *__restrict__ omega, float lam2, float *__restrict__ out,
+                  double *__restrict__ partials)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        float e;
+        out[i] = stencil_at(d, i, z, omega, lam2, e);
+        acc += (double)e;
+    }
+    if (NORM) block_sum_store(acc, partials);
+}
+
+__global__ void __launch_bounds__(kThreads)
+reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
+                   const float *__restrict__ omega, float lam2, const float *__restrict__ c,
+                   float *__restrict__ g, float *__restrict__ s, int first,
+                   double *__restrict__ partials)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        float e;
+        const float gn = c[i] - stencil_at(d, i, x, omega, lam2, e);
+        float sn;
+        if (first) {
+            sn = gn;
+        } else {
+            sn = s[i] + (gn - g[i]);
+        }
+        g[i] = gn;
+        s[i] = sn;
+        acc += (double)sn * (double)sn;
+    }
+    if (partials) block_sum_store(acc, partials);
+}
+
+}  // namespace
+
+int stencil_blocks(long long M)
+{
+    // persistent-style grid: 152 SMs x 8 resident CTAs of 256 threads
+    long long want = (M + kThreads - 1) / kThreads;
+    const long long cap = 152LL * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_weights(VolDims d, const float *x, const float *xp, float alpha2,
+                           float lambda2, float tau2, int rule, int variant, float *omega,
+                           float *w2sq, cudaStream_t st)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    weights_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, x, xp, alpha2, lambda2, tau2,
+                                                          rule, variant, omega, w2sq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prior_rhs(VolDims d, const float *xp, const float *w2sq, float lambda2,
+                             int variant, float *c, cudaStream_t st)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    prior_rhs_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, xp, w2sq, lambda2, variant, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_normal(VolDims d, const float *z, const float *omega, float lam2_piple,
+                              float *out, double *partials, cudaStream_t st)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    if (partials)
+        reg_normal_kernel<true><<<stencil_blocks(M), kThreads, 0, st>>>(d, M, z, omega,
+                                                                       lam2_piple, out, partials);
+    else
+        reg_normal_kernel<false><<<stencil_blocks(M), kThreads, 0, st>>>(d, M, z, omega,
+                                                                        lam2_piple, out, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, float lam2_piple,
+                               const float *c, float *g, float *s, int first, double *partials,
+                               cudaStream_t st)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    reg_restart_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, x, omega, lam2_piple, c, g,
+                                                              s, first, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace piccs

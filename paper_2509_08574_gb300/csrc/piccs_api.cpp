@@ -1,0 +1,572 @@
+// Host side of libpiccs: the C ABI of include/piccs.h.
+//
+// It validates arguments, builds the per-view ray tables in FP64, owns the
+// device workspace and enqueues the IRN-PICCS iteration (Sec. 2.3) on the
+// context's stream.  Every step of the arithmetic runs in the CUDA kernels of
+// this library; the host only orders launches.  The Krylov scalars stay on
+// the device, so a whole reconstruction is enqueued without a round trip.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/piccs.h"
+#include "internal.h"
+#include "ray_tables.h"
+
+using namespace piccs;
+
+struct piccs_ctx {
+    piccs_geometry geo;           // angles_rad points into `angles`
+    std::vector<double> angles;
+    ProjGeom pg;
+    VolDims vd;
+    long long M = 0, N = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool has_prior = false;
+    std::string err;
+
+    // device workspace (one allocation, carved up)
+    void *base = nullptr;
+    size_t bytes = 0;
+    ColParams *cols = nullptr;
+    float *vrow = nullptr;
+    float *xprior = nullptr, *x = nullptr, *p = nullptr, *s = nullptr, *g = nullptr,
+          *t = nullptr, *omega = nullptr, *c = nullptr, *w2sq = nullptr;
+    float *r = nullptr, *q = nullptr, *bstage = nullptr;
+    double *part_fwd = nullptr, *part_vol = nullptr, *part_vec = nullptr;
+    int n_part_fwd = 0, n_part_vol = 0, n_part_vec = 0;
+    KrylovScalars *ks = nullptr;
+    int *flag = nullptr;
+    double *dsum = nullptr;
+
+    // kernel accounting
+    bool timing = false;
+    long long launches[PICCS_KERNEL_CLASSES] = {};
+    double total_ms[PICCS_KERNEL_CLASSES] = {};
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int set_err(piccs_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                               \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err((ctx), PICCS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+cudaEvent_t take_event(piccs_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Counts one kernel launch of class `kind` and, with timing on, brackets it
+// with two events on the context's stream.
+struct Launch {
+    piccs_ctx *ctx;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Launch(piccs_ctx *c, int k) : ctx(c), kind(k)
+    {
+        ctx->launches[kind] += 1;
+        if (ctx->timing) {
+            a = take_event(ctx);
+            if (a) cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~Launch()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            if (b) {
+                cudaEventRecord(b, ctx->stream);
+                ctx->pending.push_back({kind, a, b});
+            } else {
+                ctx->event_pool.push_back(a);
+            }
+        }
+    }
+};
+
+#define LAUNCH(ctx, kind, call)                          \
+    do {                                                 \
+        Launch l_((ctx), (kind));                        \
+        CUDA_TRY((ctx), (call));                         \
+    } while (0)
+
+int check_geometry(const piccs_geometry *g, char *why, size_t n)
+{
+    if (!g) { snprintf(why, n, "geometry is NULL"); return PICCS_EINVAL; }
+    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) { snprintf(why, n, "volume size must be positive"); return PICCS_EINVAL; }
+    if (g->nu <= 0 || g->nv <= 0) { snprintf(why, n, "detector size must be positive"); return PICCS_EINVAL; }
+    if (g->n_views <= 0) { snprintf(why, n, "n_views must be positive"); return PICCS_EINVAL; }
+    // sizes below 1e-4 mm would push the FP32 crossing parameters out of range
+    if (!finite_pos(g->vx) || !finite_pos(g->vy) || !finite_pos(g->vz) || g->vx < 1e-4 || g->vy < 1e-4 || g->vz < 1e-4) { snprintf(why, n, "voxel size must be finite and >= 1e-4 mm"); return PICCS_EINVAL; }
+    if (!finite_pos(g->du) || !finite_pos(g->dv) || g->du < 1e-4 || g->dv < 1e-4) { snprintf(why, n, "detector pitch must be finite and >= 1e-4 mm"); return PICCS_EINVAL; }
+    if (!(g->dsd < 1e7)) { snprintf(why, n, "dsd must be below 1e7 mm"); return PICCS_EINVAL; }
+    const double M = (double)g->nx * g->ny * g->nz;
+    const double N = (double)g->n_views * g->nu * g->nv;
+    if (M >= 2147483648.0) { snprintf(why, n, "nx*ny*nz = %.0f exceeds 2^31-1", M); return PICCS_EINVAL; }
+    if (N >= 2147483648.0) { snprintf(why, n, "n_views*nu*nv = %.0f exceeds 2^31-1", N); return PICCS_EINVAL; }
+    if (!g->angles_rad) { snprintf(why, n, "angles_rad is NULL"); return PICCS_EINVAL; }
+    for (int j = 0; j < g->n_views; ++j)
+        if (!std::isfinite(g->angles_rad[j])) { snprintf(why, n, "angle %d is not finite", j); return PICCS_EINVAL; }
+    if (g->proj_layout != PICCS_LAYOUT_UV && g->proj_layout != PICCS_LAYOUT_VU) { snprintf(why, n, "unknown proj_layout %d", g->proj_layout); return PICCS_EINVAL; }
+    const double R = 0.5 * std::sqrt((g->nx * g->vx) * (g->nx * g->vx) + (g->ny * g->vy) * (g->ny * g->vy));
+    if (!std::isfinite(g->dso) || !(g->dso > R)) { snprintf(why, n, "dso=%g must exceed the volume's circumscribed radius %g", g->dso, R); return PICCS_EINVAL; }
+    if (!std::isfinite(g->dsd) || !(g->dsd - g->dso > R)) { snprintf(why, n, "dsd-dso=%g must exceed the volume's circumscribed radius %g", g->dsd - g->dso, R); return PICCS_EINVAL; }
+    return PICCS_OK;
+}
+
+int check_params(const piccs_params *p, char *why, size_t n)
+{
+    if (!p) { snprintf(why, n, "params is NULL"); return PICCS_EINVAL; }
+    if (!std::isfinite(p->alpha) || p->alpha < 0.f) { snprintf(why, n, "alpha must be finite and >= 0"); return PICCS_EINVAL; }
+    if (!std::isfinite(p->lambda) || p->lambda < 0.f) { snprintf(why, n, "lambda must be finite and >= 0"); return PICCS_EINVAL; }
+    if (!std::isfinite(p->tau) || !(p->tau > 0.f)) { snprintf(why, n, "tau must be finite and > 0"); return PICCS_EINVAL; }
+    if (p->n_outer < 1 || p->n_inner < 0) { snprintf(why, n, "need n_outer >= 1 and n_inner >= 0"); return PICCS_EINVAL; }
+    if ((long long)p->n_outer * (p->n_inner + 1) > 512) { snprintf(why, n, "n_outer*(n_inner+1) must be <= 512"); return PICCS_EINVAL; }
+    if (p->variant < 0 || p->variant > 3) { snprintf(why, n, "unknown variant %d", p->variant); return PICCS_EINVAL; }
+    if (p->weight_rule < 0 || p->weight_rule > 1) { snprintf(why, n, "unknown weight_rule %d", p->weight_rule); return PICCS_EINVAL; }
+    if (p->x0_mode < 0 || p->x0_mode > 2) { snprintf(why, n, "unknown x0_mode %d", p->x0_mode); return PICCS_EINVAL; }
+    return PICCS_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t off_cols, off_vrow, off_img[9], off_r, off_q, off_b, off_pf, off_pv, off_pvec, off_ks,
+        off_flag, off_dsum, total;
+    int n_pf, n_pv, n_pvec;
+};
+
+Layout plan(const piccs_geometry *g)
+{
+    Layout L{};
+    const size_t M = (size_t)g->nx * g->ny * g->nz;
+    const size_t N = (size_t)g->n_views * g->nu * g->nv;
+    ProjGeom pg{};
+    pg.nx = g->nx; pg.ny = g->ny; pg.nz = g->nz; pg.nu = g->nu; pg.nv = g->nv; pg.n_views = g->n_views;
+    L.n_pf = project_blocks(pg);
+    L.n_pv = stencil_blocks((long long)M);
+    L.n_pvec = vector_blocks();
+    size_t o = 0;
+    L.off_cols = o; o += align256((size_t)g->n_views * g->nu * sizeof(ColParams));
+    L.off_vrow = o; o += align256((size_t)g->nv * sizeof(float));
+    for (int i = 0; i < 9; ++i) { L.off_img[i] = o; o += align256(M * sizeof(float)); }
+    L.off_r = o; o += align256(N * sizeof(float));
+    L.off_q = o; o += align256(N * sizeof(float));
+    L.off_b = o; o += align256(N * sizeof(float));
+    L.off_pf = o; o += align256((size_t)L.n_pf * sizeof(double));
+    L.off_pv = o; o += align256((size_t)L.n_pv * sizeof(double));
+    L.off_pvec = o; o += align256((size_t)L.n_pvec * sizeof(double));
+    L.off_ks = o; o += align256(sizeof(KrylovScalars));
+    L.off_flag = o; o += align256(sizeof(int));
+    L.off_dsum = o; o += align256(sizeof(double));
+    L.total = o;
+    return L;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *piccs_last_error(const piccs_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_create_err.c_str();
+}
+
+int piccs_validate(const piccs_geometry *geometry, const piccs_params *params)
+{
+    char why[256];
+    int rc = check_geometry(geometry, why, sizeof why);
+    if (rc == PICCS_OK && params) rc = check_params(params, why, sizeof why);
+    if (rc != PICCS_OK) return set_err(nullptr, rc, "%s", why);
+    return PICCS_OK;
+}
+
+int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
+                          size_t *bytes)
+{
+    int rc = piccs_validate(geometry, params);
+    if (rc != PICCS_OK) return rc;
+    if (!bytes) return set_err(nullptr, PICCS_EINVAL, "bytes is NULL");
+    *bytes = plan(geometry).total;
+    return PICCS_OK;
+}
+
+int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_stream)
+{
+    if (!out) return set_err(nullptr, PICCS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = piccs_validate(geometry, nullptr);
+    if (rc != PICCS_OK) return rc;
+    const Layout L = plan(geometry);
+
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess)
+        return set_err(nullptr, PICCS_ECUDA, "cudaMemGetInfo failed: %s", cudaGetErrorString(e));
+    if (L.total + (64u << 20) > free_b)
+        return set_err(nullptr, PICCS_ENOMEM, "workspace needs %zu bytes, %zu free", L.total, free_b);
+
+    piccs_ctx *ctx = new (std::nothrow) piccs_ctx();
+    if (!ctx) return set_err(nullptr, PICCS_ENOMEM, "host allocation failed");
+    ctx->geo = *geometry;
+    ctx->angles.assign(geometry->angles_rad, geometry->angles_rad + geometry->n_views);
+    ctx->geo.angles_rad = ctx->angles.data();
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&ctx->device);
+    const piccs_geometry &g = ctx->geo;
+    ctx->M = (long long)g.nx * g.ny * g.nz;
+    ctx->N = (long long)g.n_views * g.nu * g.nv;
+    ctx->pg.nx = g.nx; ctx->pg.ny = g.ny; ctx->pg.nz = g.nz;
+    ctx->pg.nu = g.nu; ctx->pg.nv = g.nv; ctx->pg.n_views = g.n_views;
+    if (g.proj_layout == PICCS_LAYOUT_UV) {
+        ctx->pg.sv = 1; ctx->pg.su = g.nv;
+    } else {
+        ctx->pg.su = 1; ctx->pg.sv = g.nu;
+    }
+    ctx->pg.sj = (long long)g.nu * g.nv;
+    ctx->pg.halfnz = 0.5f * (float)g.nz;
+    ctx->vd = VolDims{g.nx, g.ny, g.nz};
+
+    e = cudaMalloc(&ctx->base, L.total);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return set_err(nullptr, PICCS_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+    }
+    ctx->bytes = L.total;
+    char *b = static_cast<char *>(ctx->base);
+    ctx->cols = reinterpret_cast<ColParams *>(b + L.off_cols);
+    ctx->vrow = reinterpret_cast<float *>(b + L.off_vrow);
+    float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
+                      &ctx->t, &ctx->omega, &ctx->c, &ctx->w2sq};
+    for (int i = 0; i < 9; ++i) *img[i] = reinterpret_cast<float *>(b + L.off_img[i]);
+    ctx->r = reinterpret_cast<float *>(b + L.off_r);
+    ctx->q = reinterpret_cast<float *>(b + L.off_q);
+    ctx->bstage = reinterpret_cast<float *>(b + L.off_b);
+    ctx->part_fwd = reinterpret_cast<double *>(b + L.off_pf);
+    ctx->part_vol = reinterpret_cast<double *>(b + L.off_pv);
+    ctx->part_vec = reinterpret_cast<double *>(b + L.off_pvec);
+    ctx->n_part_fwd = L.n_pf;
+    ctx->n_part_vol = L.n_pv;
+    ctx->n_part_vec = L.n_pvec;
+    ctx->ks = reinterpret_cast<KrylovScalars *>(b + L.off_ks);
+    ctx->flag = reinterpret_cast<int *>(b + L.off_flag);
+    ctx->dsum = reinterpret_cast<double *>(b + L.off_dsum);
+
+    std::vector<ColParams> cols;
+    std::vector<float> vrow;
+    build_tables(&g, cols, vrow);
+    e = cudaMemcpy(ctx->cols, cols.data(), cols.size() * sizeof(ColParams), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->vrow, vrow.data(), vrow.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->ks, 0, sizeof(KrylovScalars));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->base);
+        delete ctx;
+        return set_err(nullptr, PICCS_ECUDA, "table upload failed: %s", cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return PICCS_OK;
+}
+
+void piccs_destroy(piccs_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    cudaFree(ctx->base);
+    delete ctx;
+}
+
+int piccs_profile_enable(piccs_ctx *ctx, int timing)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &p : ctx->pending) {
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
+        ctx->launches[k] = 0;
+        ctx->total_ms[k] = 0.0;
+    }
+    ctx->timing = timing != 0;
+    return PICCS_OK;
+}
+
+int piccs_profile_read(piccs_ctx *ctx, piccs_profile *out)
+{
+    if (!ctx || !out) return set_err(ctx, PICCS_EINVAL, "NULL argument");
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) ctx->total_ms[p.kind] += ms;
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    std::memset(out, 0, sizeof *out);
+    for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
+        out->launches[k] = ctx->launches[k];
+        out->total_ms[k] = ctx->total_ms[k];
+        out->total_launches += ctx->launches[k];
+    }
+    return PICCS_OK;
+}
+
+int piccs_set_stream(piccs_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return PICCS_OK;
+}
+
+int piccs_set_prior(piccs_ctx *ctx, const float *d_xprior)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (!d_xprior) return set_err(ctx, PICCS_EINVAL, "d_xprior is NULL");
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->xprior, d_xprior, ctx->M * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(ctx->M, ctx->xprior, ctx->flag, ctx->stream));
+    int bad = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad) {
+        ctx->has_prior = false;
+        return set_err(ctx, PICCS_ENONFINITE, "prior volume holds NaN or Inf");
+    }
+    ctx->has_prior = true;
+    return PICCS_OK;
+}
+
+int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, d_vol, d_proj, FWD_PLAIN, nullptr,
+                                 nullptr, nullptr, ctx->stream));
+    return PICCS_OK;
+}
+
+int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
+    CUDA_TRY(ctx, cudaMemsetAsync(d_vol, 0, ctx->M * sizeof(float), ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, d_proj, d_vol, ctx->stream));
+    return PICCS_OK;
+}
+
+static float lam2_piple(const piccs_params *p)
+{
+    return p->variant == PICCS_VARIANT_PIPLE ? p->lambda * p->lambda : 0.f;
+}
+
+static int enqueue_weights(piccs_ctx *ctx, const float *d_x, const piccs_params *p, float *omega,
+                           float *c)
+{
+    const float a2 = p->alpha * p->alpha, l2 = p->lambda * p->lambda;
+    const float tau2 = p->tau * p->tau;
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_weights(ctx->vd, d_x, ctx->xprior, a2, l2, tau2, p->weight_rule,
+                                 p->variant, omega, ctx->w2sq, ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_prior_rhs(ctx->vd, ctx->xprior, ctx->w2sq, l2, p->variant, c, ctx->stream));
+    return PICCS_OK;
+}
+
+static bool needs_prior(const piccs_params *p)
+{
+    return p->variant == PICCS_VARIANT_PICCS || p->variant == PICCS_VARIANT_PIPLE ||
+           p->x0_mode == PICCS_X0_PRIOR;
+}
+
+int piccs_reg_weights(piccs_ctx *ctx, const float *d_x, const piccs_params *params,
+                      float *d_omega, float *d_c)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    char why[256];
+    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(ctx, PICCS_EINVAL, "%s", why);
+    if (!d_x || !d_omega || !d_c) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
+    if ((params->variant == PICCS_VARIANT_PICCS || params->variant == PICCS_VARIANT_PIPLE) &&
+        !ctx->has_prior)
+        return set_err(ctx, PICCS_EINVAL, "prior not set");
+    return enqueue_weights(ctx, d_x, params, d_omega, d_c);
+}
+
+int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *params,
+                     const float *d_z, float *d_out, double *h_rho)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    char why[256];
+    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(ctx, PICCS_EINVAL, "%s", why);
+    if (!d_omega || !d_z || !d_out) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, d_z, d_omega, lam2_piple(params), d_out,
+                                    h_rho ? ctx->part_vol : nullptr, ctx->stream));
+    if (h_rho) {
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_sum_partials(ctx->part_vol, ctx->n_part_vol, ctx->dsum, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(h_rho, ctx->dsum, sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return PICCS_OK;
+}
+
+// One IRN-PICCS reconstruction from device-resident data d_b into ctx->x.
+static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
+                               const float *d_x0)
+{
+    cudaStream_t st = ctx->stream;
+    const long long M = ctx->M, N = ctx->N;
+    const float l2p = lam2_piple(p);
+
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st));
+    if (p->x0_mode == PICCS_X0_PRIOR) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, ctx->xprior, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    } else if (p->x0_mode == PICCS_X0_ZERO) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->x, 0, M * sizeof(float), st));
+    } else {
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, d_x0, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    // data residual r = b - A x0 (also flags NaN/Inf in b)
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->x, ctx->r, FWD_RESID, d_b,
+                                 nullptr, &ctx->ks->nonfinite, st));
+    for (int k = 0; k < p->n_outer; ++k) {
+        // reweighting at the previous iterate (Eqs. 10-11)
+        int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c);
+        if (rc != PICCS_OK) return rc;
+        // restart: g = c - D^T Omega D x, s = A^T r + g
+        if (k == 0) {
+            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
+                                             ctx->s, 1, nullptr, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->r, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st));
+        } else {
+            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
+                                             ctx->s, 0, ctx->part_vol, st));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vol, ctx->n_part_vol, 1, st));
+        }
+        for (int it = 0; it < p->n_inner; ++it) {
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st));
+            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st));
+            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->p, ctx->q, FWD_PLAIN,
+                                         nullptr, ctx->part_fwd, nullptr, st));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
+                                                ctx->part_vol, ctx->n_part_vol, st));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
+                                          ctx->q, ctx->ks, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->r, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st));
+        }
+    }
+    return PICCS_OK;
+}
+
+static int check_reconstruct_args(piccs_ctx *ctx, const void *proj, const piccs_params *params,
+                                  const void *x0, const void *out)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    char why[256];
+    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(ctx, PICCS_EINVAL, "%s", why);
+    if (!proj || !out) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
+    if (params->x0_mode == PICCS_X0_USER && !x0) return set_err(ctx, PICCS_EINVAL, "x0_mode USER needs x0");
+    if (needs_prior(params) && !ctx->has_prior) return set_err(ctx, PICCS_EINVAL, "prior not set");
+    return PICCS_OK;
+}
+
+int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *params,
+                      const float *d_x0, float *d_vol_out)
+{
+    int rc = check_reconstruct_args(ctx, d_proj, params, d_x0, d_vol_out);
+    if (rc != PICCS_OK) return rc;
+    rc = enqueue_reconstruct(ctx, d_proj, params, d_x0);
+    if (rc != PICCS_OK) return rc;
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_vol_out, ctx->x, ctx->M * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    return PICCS_OK;
+}
+
+int piccs_report(piccs_ctx *ctx, piccs_stats *out)
+{
+    if (!ctx || !out) return set_err(ctx, PICCS_EINVAL, "NULL argument");
+    KrylovScalars ks;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpy(&ks, ctx->ks, sizeof ks, cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof *out);
+    out->status = ks.nonfinite ? PICCS_ENONFINITE : ks.status;
+    out->iterations_run = ks.iters_run;
+    out->n_history = ks.n_hist < 512 ? ks.n_hist : 512;
+    std::memcpy(out->gamma_history, ks.hist, sizeof(double) * out->n_history);
+    return PICCS_OK;
+}
+
+int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_params *params,
+                           const float *h_x0, float *h_vol_out)
+{
+    int rc = check_reconstruct_args(ctx, h_proj, params, h_x0, h_vol_out);
+    if (rc != PICCS_OK) return rc;
+    cudaStream_t st = ctx->stream;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->bstage, h_proj, ctx->N * sizeof(float), cudaMemcpyHostToDevice, st));
+    const float *dx0 = nullptr;
+    if (params->x0_mode == PICCS_X0_USER) {
+        // the initial guess goes through the p buffer, which is free until the first step
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->p, h_x0, ctx->M * sizeof(float), cudaMemcpyHostToDevice, st));
+        dx0 = ctx->p;
+    }
+    rc = enqueue_reconstruct(ctx, ctx->bstage, params, dx0);
+    if (rc != PICCS_OK) return rc;
+    CUDA_TRY(ctx, cudaMemcpyAsync(h_vol_out, ctx->x, ctx->M * sizeof(float), cudaMemcpyDeviceToHost, st));
+    piccs_stats rep;
+    rc = piccs_report(ctx, &rep);
+    if (rc != PICCS_OK) return rc;
+    if (rep.status != PICCS_OK)
+        return set_err(ctx, rep.status, rep.status == PICCS_ENONFINITE ? "projections hold NaN or Inf"
+                                                                       : "Krylov breakdown");
+    return PICCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+"""C ABI of libpiccs without a GPU: the library loads, exports every entry
+point include/piccs.h declares, and its pure-host calls (argument validation,
+workspace sizing) behave.  No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import phantoms as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(piccs_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import paper_2509_08574_gb300 as pk
+    return pk
+
+
+def test_every_declared_symbol_is_exported(pk):
+    names = _declared()
+    assert len(names) >= 14
+    lib = pk.library()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(pk.EXPORTED) | {"piccs_report"}
+
+
+def test_validate_accepts_the_workloads(pk):
+    for scan in (P.c1_small(), P.c2_needle(), P.c3_sphere_growth(), P.c5_carm()):
+        pk.piccs_validate(scan.geometry, pk.make_params())
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(nv=-1), dict(vx=0.0), dict(du=float("nan")), dict(dso=10.0),
+    dict(dsd=1040.0), dict(layout=7), dict(angles=np.array([0.0, np.inf])),
+])
+def test_validate_rejects_bad_geometry(pk, bad):
+    g = P.c1_small().geometry.replace(**bad)
+    with pytest.raises(pk.PiccsError) as e:
+        pk.piccs_validate(g)
+    assert e.value.code == pk.PICCS_EINVAL
+    assert pk.piccs_last_error()
+
+
+def test_validate_rejects_sizes_beyond_int32(pk):
+    g = P.c1_small().geometry.replace(nx=2048, ny=2048, nz=1024, vx=0.01, vy=0.01, vz=0.01)
+    with pytest.raises(pk.PiccsError):
+        pk.piccs_validate(g)
+
+
+@pytest.mark.parametrize("kw", [dict(tau=0.0), dict(alpha=-1.0), dict(n_outer=0),
+                                dict(variant=9), dict(weight_rule=3), dict(x0_mode=5),
+                                dict(n_outer=100, n_inner=10)])
+def test_validate_rejects_bad_params(pk, kw):
+    with pytest.raises(pk.PiccsError) as e:
+        pk.piccs_validate(P.c1_small().geometry, pk.make_params(**kw))
+    assert e.value.code == pk.PICCS_EINVAL
+
+
+def test_workspace_size(pk):
+    g = P.c2_needle().geometry
+    b = pk.piccs_query_workspace(g)
+    M, N = g.M, g.N
+    # nine image vectors and three data vectors dominate
+    assert 4 * (9 * M + 3 * N) <= b <= 4 * (9 * M + 3 * N) + (16 << 20)
