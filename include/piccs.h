@@ -202,6 +202,34 @@ int piccs_profile_enable(piccs_ctx *ctx, int timing);
  * piccs_profile_enable.  Synchronises. */
 int piccs_profile_read(piccs_ctx *ctx, piccs_profile *out);
 
+/* Allocation-free form of piccs_reg_normal for callers that cannot allocate
+ * device memory -- code living inside a host application whose memory pool
+ * owns the whole GPU under a hard cap, or a latency-critical loop where a
+ * cudaMalloc/cudaFree would synchronise the device.  It needs no context:
+ * it computes d_out = D^T diag(d_omega) D d_z + lambda2_piple * d_z and
+ * *d_rho = sum_i omega_i |(D z)_i|^2 + lambda2_piple |z|^2 for an nx*ny*nz
+ * z-fastest FP32 volume (lambda2_piple = lambda^2 for PIPLE, else 0), on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream).  d_omega, d_z,
+ * d_out (M floats) and d_rho (one double) are caller-owned device buffers.
+ * The paper has no counterpart: this is a deployment variant of the
+ * regularisation step of Sec. 2.3.
+ *   Scratch: the per-CTA FP64 partial sums live in a 32 KiB (4096 doubles)
+ *   array inside libpiccs that every GPU loading the library holds until
+ *   exit; volumes of any size up to 2^31-1 voxels use at most 1216 entries,
+ *   larger ones are rejected with PICCS_EINVAL.  Nothing is allocated or
+ *   freed (no cudaMalloc, cudaFree or allocating library routine).
+ *   The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  All calls share the array and it keeps the last call's
+ *   contents (every call overwrites what it reads, so nothing needs
+ *   clearing); calls whose kernels overlap on the GPU, e.g. from two
+ *   streams, race on it and must be serialised by the caller.
+ *   Errors: PICCS_EINVAL / PICCS_ECUDA, message via piccs_last_error(NULL).
+ *   Asynchronous with respect to the host. */
+int piccs_reg_normal_noalloc(int nx, int ny, int nz, const float *d_omega,
+                             float lambda2_piple, const float *d_z, float *d_out,
+                             double *d_rho, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

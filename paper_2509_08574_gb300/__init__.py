@@ -94,6 +94,7 @@ def _load():
         "piccs_reg_normal": (i, [vp, vp, P, vp, vp, C.POINTER(d)]),
         "piccs_profile_enable": (i, [vp, i]),
         "piccs_profile_read": (i, [vp, C.POINTER(piccs_profile)]),
+        "piccs_reg_normal_noalloc": (i, [i, i, i, vp, C.c_float, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -107,7 +108,7 @@ EXPORTED = ("piccs_create", "piccs_destroy", "piccs_last_error", "piccs_set_stre
             "piccs_query_workspace", "piccs_validate", "piccs_set_prior", "piccs_reconstruct",
             "piccs_reconstruct_host", "piccs_report", "piccs_forward", "piccs_adjoint",
             "piccs_reg_weights", "piccs_reg_normal", "piccs_profile_enable",
-            "piccs_profile_read")
+            "piccs_profile_read", "piccs_reg_normal_noalloc")
 
 
 def library():
@@ -248,6 +249,23 @@ def piccs_reg_normal(ctx, d_omega, params, d_z, d_out, want_rho=True):
     _check(_lib.piccs_reg_normal(ctx, _ptr(d_omega, what="omega"), C.byref(params), _ptr(d_z, what="z"),
                                  _ptr(d_out, what="out"), C.byref(rho) if want_rho else None), ctx)
     return float(rho.value) if want_rho else None
+
+
+def piccs_reg_normal_noalloc(nx, ny, nz, d_omega, lambda2_piple, d_z, d_out, d_rho,
+                             stream=None):
+    """Context-free, allocation-free D^T diag(omega) D z (+ lambda2_piple z) and
+    its energy, for callers that cannot allocate device memory; d_rho is a
+    device buffer of one float64.  See include/piccs.h."""
+    n = int(nx) * int(ny) * int(nz)
+    if hasattr(d_rho, "data_ptr"):
+        if str(d_rho.dtype) != "torch.float64" or d_rho.numel() < 1:
+            raise TypeError("d_rho must be a float64 device tensor")
+        rho_ptr = d_rho.data_ptr()
+    else:
+        rho_ptr = d_rho
+    _check(_lib.piccs_reg_normal_noalloc(int(nx), int(ny), int(nz), _ptr(d_omega, n, "omega"),
+                                         float(lambda2_piple), _ptr(d_z, n, "z"),
+                                         _ptr(d_out, n, "out"), rho_ptr, _stream_handle(stream)))
 
 
 def piccs_profile_enable(ctx, timing=True):

@@ -99,4 +99,8 @@ cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st);
 cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st);
 cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st);
 
+// ---- host helpers (piccs_api.cpp) ----
+// Sets the per-thread message that piccs_last_error(NULL) returns.
+void set_thread_error(const char *msg);
+
 }  // namespace piccs

@@ -203,6 +203,8 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 }  // namespace
 
+void piccs::set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
+
 extern "C" {
 
 const char *piccs_last_error(const piccs_ctx *ctx)
