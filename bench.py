@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="run only the projector pair on the workload (for profiler captures)")
     return ap.parse_args()
 
 
@@ -360,8 +362,42 @@ def run_ours(args):
     return 0
 
 
+def run_kernels_only(args):
+    """A (forward) and A^T (adjoint) launches on the 256^3 workload, each
+    preceded by an L2 flush; prints their CUDA-event times."""
+    import torch
+    import paper_2509_08574_gb300 as pk
+
+    scan = workload()
+    g = scan.geometry
+    x = torch.from_numpy(scan.prior_volume(ss=1)).cuda()
+    y = torch.from_numpy(P.random_projections(g, 7).astype(np.float32)).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    q = torch.empty(g.proj_shape(), dtype=torch.float32, device="cuda")
+    s = torch.empty(g.vol_shape(), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    with pk.Context(g, stream=stream) as ctx:
+        times = {"forward": [], "adjoint": []}
+        for _ in range(max(args.steps, 1)):
+            for kind in ("forward", "adjoint"):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if kind == "forward":
+                    ctx.forward(x, q)
+                else:
+                    ctx.adjoint(y, s)
+                e1.record()
+                torch.cuda.synchronize()
+                times[kind].append(e0.elapsed_time(e1))
+    print(json.dumps({k: {"ms": v} for k, v in times.items()}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.kernels_only:
+        return run_kernels_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -10,31 +10,36 @@ namespace piccs {
 // Per (view, detector column) ray-walk constants, computed in FP64 on the host
 // and rounded once.  All rays of one detector column share their projection
 // onto the xy plane (the detector v axis is parallel to the rotation axis and
-// the source lies in z = 0), so the xy part of the Siddon walk is identical
-// for the whole column; only the z crossings depend on the row.
-//
-// The xy walk is parametrised by s = xy distance (mm) from the point where the
-// column's rays enter the volume's xy square:
-//   x plane k (voxel units, 0..nx) is crossed at s = (k - ex) * inv_dx,
-//   y plane k                        at s = (k - ey) * inv_dy,
-//   the square is left at s = L.
-// (ex, ey) is the entry point in voxel units and (ix0, iy0) = floor of it,
-// so the first crossing ahead is never behind s = 0.  A direction parallel to
-// the x planes has inv_dx = +inf and ex = -1e30 (every crossing at +inf).
-// Row v (detector height, mm) has z (voxel units, centred) = v * kE + s / (KD / v)
-// and 3D length per unit s of sqrt(1 + (v * invD)^2).
+// the source lies in z = 0), so the xy part of the Siddon walk is the same for
+// the whole column and is stored once as a cell table (see ray_tables.h):
+// cells[start4*4 + c], c < ncells, is the xy distance (mm, from the column's
+// entry into the volume's xy square) at which the rays leave cell c, with the
+// sign bit set when the next cell is one step in y (else one step in x).  The
+// walk starts in voxel column (ix0, iy0) at distance 0.
+// Row v (detector height, mm) has z (voxel units, centred) = v * (kE + s * rKD),
+// crosses the z plane with centred coordinate kc at s = (kc - v*kE) * (KD * rv)
+// where rv = 1/v (rv = 1e30 for v = 0: such a row never crosses a z plane), and
+// has 3D length per unit s of sqrt(1 + (v * invD)^2).
 struct __align__(16) ColParams {
-    float inv_dx, ex, inv_dy, ey;
-    float L, kE, KD, invD;
-    int ix0, iy0, stepx, stepy;
-    int pad0, pad1, pad2, pad3;
+    long long start4;        // float4 index of the column's first cell
+    int ncells;              // 0: the column misses the volume
+    int ix0;
+    int iy0, stepx, stepy, pad0;
+    float kE, KD, invD, rKD; // one 16-byte load for the adjoint's gather
 };
+
+// One crossing of an xy voxel column by a detector column (the transpose of
+// the column cell tables): x = view << 16 | detector column, y/z = the bits of
+// the FP32 xy distances at which the column's rays enter and leave the voxel
+// column (the same values the forward walk uses), w unused.
+typedef int4 CellHit;
 
 struct ProjGeom {
     int nx, ny, nz;
     int nu, nv, n_views;
     long long sj, su, sv;   // projection strides of view, column, row
     float halfnz;           // nz / 2
+    float rdv, cv;          // 1 / dv and (nv - 1) / 2: row index of height v = v * rdv + cv
 };
 
 // Device-side Krylov scalars (FP64), read by every vector kernel so that no
@@ -59,11 +64,14 @@ enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1 };
 // ---- projector (kernels_project.cu) ----
 int project_blocks(const ProjGeom &g);
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *vol, float *out, int mode, const float *b,
-                           double *partials, int *nonfinite, cudaStream_t st);
-// vol += A^T proj (vol must hold the starting values, e.g. zeros)
+                           const float *rvrow, const float *cells, const float *vol, float *out,
+                           int mode,
+                           const float *b, double *partials, int *nonfinite, cudaStream_t st);
+// vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
+// N-float scratch that receives proj scaled by each ray's sec.
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *proj, float *vol, cudaStream_t st);
+                           const float *rvrow, const int *hit_ptr, const CellHit *hits,
+                           const float *proj, float *rs, float *vol, cudaStream_t st);
 
 // ---- regulariser (kernels_reg.cu) ----
 struct VolDims { int nx, ny, nz; };

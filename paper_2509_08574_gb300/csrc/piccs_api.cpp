@@ -36,10 +36,13 @@ struct piccs_ctx {
     void *base = nullptr;
     size_t bytes = 0;
     ColParams *cols = nullptr;
-    float *vrow = nullptr;
+    float *vrow = nullptr, *rvrow = nullptr;
+    float *cells = nullptr;
+    int *hit_ptr = nullptr;
+    CellHit *hits = nullptr;
     float *xprior = nullptr, *x = nullptr, *p = nullptr, *s = nullptr, *g = nullptr,
           *t = nullptr, *omega = nullptr, *c = nullptr, *w2sq = nullptr;
-    float *r = nullptr, *q = nullptr, *bstage = nullptr;
+    float *r = nullptr, *q = nullptr, *bstage = nullptr, *rs = nullptr;
     double *part_fwd = nullptr, *part_vol = nullptr, *part_vec = nullptr;
     int n_part_fwd = 0, n_part_vol = 0, n_part_vec = 0;
     KrylovScalars *ks = nullptr;
@@ -143,6 +146,8 @@ int check_geometry(const piccs_geometry *g, char *why, size_t n)
     if (!g->angles_rad) { snprintf(why, n, "angles_rad is NULL"); return PICCS_EINVAL; }
     for (int j = 0; j < g->n_views; ++j)
         if (!std::isfinite(g->angles_rad[j])) { snprintf(why, n, "angle %d is not finite", j); return PICCS_EINVAL; }
+    if (g->n_views > 32767 || g->nu > 65535) { snprintf(why, n, "n_views must be <= 32767 and nu <= 65535"); return PICCS_EINVAL; }
+    if ((double)g->n_views * g->nu * (g->nx + g->ny - 1) >= 2147483648.0) { snprintf(why, n, "ray tables would exceed 2^31 entries"); return PICCS_EINVAL; }
     if (g->proj_layout != PICCS_LAYOUT_UV && g->proj_layout != PICCS_LAYOUT_VU) { snprintf(why, n, "unknown proj_layout %d", g->proj_layout); return PICCS_EINVAL; }
     const double R = 0.5 * std::sqrt((g->nx * g->vx) * (g->nx * g->vx) + (g->ny * g->vy) * (g->ny * g->vy));
     if (!std::isfinite(g->dso) || !(g->dso > R)) { snprintf(why, n, "dso=%g must exceed the volume's circumscribed radius %g", g->dso, R); return PICCS_EINVAL; }
@@ -167,7 +172,8 @@ int check_params(const piccs_params *p, char *why, size_t n)
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t off_cols, off_vrow, off_img[9], off_r, off_q, off_b, off_pf, off_pv, off_pvec, off_ks,
+    size_t off_cols, off_vrow, off_rvrow, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
+        off_b, off_rs, off_pf, off_pv, off_pvec, off_ks,
         off_flag, off_dsum, total;
     int n_pf, n_pv, n_pvec;
 };
@@ -185,10 +191,15 @@ Layout plan(const piccs_geometry *g)
     size_t o = 0;
     L.off_cols = o; o += align256((size_t)g->n_views * g->nu * sizeof(ColParams));
     L.off_vrow = o; o += align256((size_t)g->nv * sizeof(float));
+    L.off_rvrow = o; o += align256((size_t)g->nv * sizeof(float));
+    L.off_cells = o; o += align256((size_t)g->n_views * g->nu * cell_stride(g) * sizeof(float));
+    L.off_hitptr = o; o += align256(((size_t)g->nx * g->ny + 1) * sizeof(int));
+    L.off_hits = o; o += align256(hit_bound(g) * sizeof(CellHit));
     for (int i = 0; i < 9; ++i) { L.off_img[i] = o; o += align256(M * sizeof(float)); }
     L.off_r = o; o += align256(N * sizeof(float));
     L.off_q = o; o += align256(N * sizeof(float));
     L.off_b = o; o += align256(N * sizeof(float));
+    L.off_rs = o; o += align256(N * sizeof(float));
     L.off_pf = o; o += align256((size_t)L.n_pf * sizeof(double));
     L.off_pv = o; o += align256((size_t)L.n_pv * sizeof(double));
     L.off_pvec = o; o += align256((size_t)L.n_pvec * sizeof(double));
@@ -266,6 +277,8 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     }
     ctx->pg.sj = (long long)g.nu * g.nv;
     ctx->pg.halfnz = 0.5f * (float)g.nz;
+    ctx->pg.rdv = (float)(1.0 / g.dv);
+    ctx->pg.cv = 0.5f * (float)(g.nv - 1);
     ctx->vd = VolDims{g.nx, g.ny, g.nz};
 
     e = cudaMalloc(&ctx->base, L.total);
@@ -277,12 +290,17 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     char *b = static_cast<char *>(ctx->base);
     ctx->cols = reinterpret_cast<ColParams *>(b + L.off_cols);
     ctx->vrow = reinterpret_cast<float *>(b + L.off_vrow);
+    ctx->rvrow = reinterpret_cast<float *>(b + L.off_rvrow);
+    ctx->cells = reinterpret_cast<float *>(b + L.off_cells);
+    ctx->hit_ptr = reinterpret_cast<int *>(b + L.off_hitptr);
+    ctx->hits = reinterpret_cast<CellHit *>(b + L.off_hits);
     float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
                       &ctx->t, &ctx->omega, &ctx->c, &ctx->w2sq};
     for (int i = 0; i < 9; ++i) *img[i] = reinterpret_cast<float *>(b + L.off_img[i]);
     ctx->r = reinterpret_cast<float *>(b + L.off_r);
     ctx->q = reinterpret_cast<float *>(b + L.off_q);
     ctx->bstage = reinterpret_cast<float *>(b + L.off_b);
+    ctx->rs = reinterpret_cast<float *>(b + L.off_rs);
     ctx->part_fwd = reinterpret_cast<double *>(b + L.off_pf);
     ctx->part_vol = reinterpret_cast<double *>(b + L.off_pv);
     ctx->part_vec = reinterpret_cast<double *>(b + L.off_pvec);
@@ -294,11 +312,21 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->dsum = reinterpret_cast<double *>(b + L.off_dsum);
 
     std::vector<ColParams> cols;
-    std::vector<float> vrow;
-    build_tables(&g, cols, vrow);
+    std::vector<float> vrow, rvrow, cells;
+    std::vector<int> hit_ptr;
+    std::vector<CellHit> hits;
+    build_tables(&g, cols, vrow, rvrow, cells, hit_ptr, hits);
     e = cudaMemcpy(ctx->cols, cols.data(), cols.size() * sizeof(ColParams), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->vrow, vrow.data(), vrow.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->rvrow, rvrow.data(), rvrow.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->cells, cells.data(), cells.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->hit_ptr, hit_ptr.data(), hit_ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hits.empty())
+        e = cudaMemcpy(ctx->hits, hits.data(), hits.size() * sizeof(CellHit), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(ctx->ks, 0, sizeof(KrylovScalars));
     if (e != cudaSuccess) {
         cudaFree(ctx->base);
@@ -389,7 +417,7 @@ int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, d_vol, d_proj, FWD_PLAIN, nullptr,
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, d_vol, d_proj, FWD_PLAIN, nullptr,
                                  nullptr, nullptr, ctx->stream));
     return PICCS_OK;
 }
@@ -399,7 +427,7 @@ int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol)
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
     CUDA_TRY(ctx, cudaMemsetAsync(d_vol, 0, ctx->M * sizeof(float), ctx->stream));
-    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, d_proj, d_vol, ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, d_proj, ctx->rs, d_vol, ctx->stream));
     return PICCS_OK;
 }
 
@@ -473,7 +501,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, d_x0, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->x, ctx->r, FWD_RESID, d_b,
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,
                                  nullptr, &ctx->ks->nonfinite, st));
     for (int k = 0; k < p->n_outer; ++k) {
         // reweighting at the previous iterate (Eqs. 10-11)
@@ -483,7 +511,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         if (k == 0) {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
                                              ctx->s, 1, nullptr, st));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->r, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st));
         } else {
@@ -494,13 +522,13 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         for (int it = 0; it < p->n_inner; ++it) {
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st));
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st));
-            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->p, ctx->q, FWD_PLAIN,
+            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, ctx->p, ctx->q, FWD_PLAIN,
                                          nullptr, ctx->part_fwd, nullptr, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
                                                 ctx->part_vol, ctx->n_part_vol, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
                                           ctx->q, ctx->ks, st));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->r, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st));
         }

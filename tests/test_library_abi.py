@@ -77,5 +77,9 @@ def test_workspace_size(pk):
     g = P.c2_needle().geometry
     b = pk.piccs_query_workspace(g)
     M, N = g.M, g.N
-    # nine image vectors and three data vectors dominate
-    assert 4 * (9 * M + 3 * N) <= b <= 4 * (9 * M + 3 * N) + (16 << 20)
+    ncol = g.n_views * g.nu
+    stride = (g.nx + g.ny + 3) // 4 * 4
+    # nine image vectors, four data vectors, the column cell table (4 B per cell
+    # slot) and its transpose (16 B per crossing, bounded by nx + ny - 1 per column)
+    expect = 4 * (9 * M + 4 * N) + 4 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
+    assert expect <= b <= expect + (16 << 20)
