@@ -12,19 +12,20 @@ namespace piccs {
 // onto the xy plane (the detector v axis is parallel to the rotation axis and
 // the source lies in z = 0), so the xy part of the Siddon walk is the same for
 // the whole column and is stored once as a cell table (see ray_tables.h):
-// cells[start4*4 + c], c < ncells, is the xy distance (mm, from the column's
-// entry into the volume's xy square) at which the rays leave cell c, with the
-// sign bit set when the next cell is one step in y (else one step in x).  The
-// walk starts in voxel column (ix0, iy0) at distance 0.
-// Row v (detector height, mm) has z (voxel units, centred) = v * (kE + s * rKD),
-// crosses the z plane with centred coordinate kc at s = (kc - v*kE) * (KD * rv)
-// where rv = 1/v (rv = 1e30 for v = 0: such a row never crosses a z plane), and
-// has 3D length per unit s of sqrt(1 + (v * invD)^2).
+// cells[start2 .. start2 + ceil(ncells/2)) hold, two per 16 bytes, for every
+// xy cell the column's rays cross: the flat index of the cell's first voxel
+// ((ix*ny + iy)*nz) and the bits of the FP32 xy distance (mm, from the
+// column's entry into the volume's xy square) at which the rays leave it.  An
+// odd list is padded with a zero-length copy of its last cell.
+// Row v (detector height, mm, with rv = 1/v, or 1e30 for v = 0) has z (voxel
+// units, centred) = v * (kE + s * rKD); with inv = KD * rv and
+// off = -(v * kE) * inv it crosses the z plane with centred coordinate kc at
+// s = fma(kc, inv, off), and its 3D length per unit s is sqrt(1 + (v*invD)^2).
 struct __align__(16) ColParams {
-    long long start4;        // float4 index of the column's first cell
+    long long start2;        // int4 index of the column's first pair of cells
     int ncells;              // 0: the column misses the volume
-    int ix0;
-    int iy0, stepx, stepy, pad0;
+    int pad0;
+    int pad1, pad2, pad3, pad4;
     float kE, KD, invD, rKD; // one 16-byte load for the adjoint's gather
 };
 
@@ -63,15 +64,15 @@ enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1 };
 
 // ---- projector (kernels_project.cu) ----
 int project_blocks(const ProjGeom &g);
-cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *rvrow, const float *cells, const float *vol, float *out,
-                           int mode,
+// vr[iv] = {v, 1/v} per detector row (1e30 for v = 0)
+cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                           const int4 *cells, const float *vol, float *out, int mode,
                            const float *b, double *partials, int *nonfinite, cudaStream_t st);
 // vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
 // N-float scratch that receives proj scaled by each ray's sec.
-cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *rvrow, const int *hit_ptr, const CellHit *hits,
-                           const float *proj, float *rs, float *vol, cudaStream_t st);
+cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                           const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
+                           float *vol, cudaStream_t st);
 
 // ---- regulariser (kernels_reg.cu) ----
 struct VolDims { int nx, ny, nz; };

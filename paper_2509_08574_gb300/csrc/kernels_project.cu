@@ -11,8 +11,9 @@
 // axis is parallel to the rotation axis and the source lies in z = 0, every
 // ray of a column has the same xy path.  That path is walked once per
 // geometry on the host (FP64, ray_tables.h) and stored as the column's cell
-// list; a warp streams it with one broadcast 16-byte load per four cells, so
-// the xy part of the walk costs almost nothing and is warp-uniform.  Only the
+// list (voxel-column index and exit distance per cell); a warp streams it with
+// one broadcast 16-byte load per two cells, so the xy part of the walk costs
+// almost nothing and is warp-uniform.  Only the
 // z crossings are per lane.  At every xy cell the 32 lanes touch neighbouring
 // z voxels of one z-fastest voxel column, so the forward gathers coalesce into
 // one or two 32-byte sectors.
@@ -24,8 +25,9 @@
 // voxel, deterministic.  Both kernels evaluate the same piece lengths
 //   len = min(s_exit_xy, s_z(exit plane)) - max(s_enter_xy, s_z(entry plane))
 // from the same FP32 cell boundaries and the same plane-crossing formula
-// (never accumulated), so A^T applies bit-identical weights to A; only the
-// order of the FP32 sums differs.
+// fma(kc, inv, off), with the exact plane coordinate kc (never an accumulated
+// distance), so A^T applies bit-identical weights to A; only the order of the
+// FP32 sums differs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -36,15 +38,10 @@ namespace piccs {
 
 namespace {
 
-constexpr int kWarps = 8;        // detector columns per CTA
+constexpr int kWarps = 8;        // detector columns per CTA (forward)
+constexpr int kGatherThreads = 64;
+constexpr int kLayersPerThread = 4;
 constexpr unsigned kFull = 0xffffffffu;
-
-struct LaneRay {
-    float zE;      // centred z (voxel units) at the entry point
-    float inv_mz;  // xy distance per voxel of z (signed; +inf when v == 0)
-    float sec;     // 3D length per unit xy length
-    int stepz;
-};
 
 // per-ray factor: 3D length per unit of xy length
 __device__ __forceinline__ float ray_sec(float v, float invD)
@@ -53,22 +50,25 @@ __device__ __forceinline__ float ray_sec(float v, float invD)
     return __fsqrt_rn(fmaf(m, m, 1.f));
 }
 
-// v: row height; rv = 1/v (1e30 for v == 0, which never crosses a z plane)
-__device__ __forceinline__ LaneRay lane_ray(const ColParams &cp, float v, float rv)
+// z-crossing constants of row {v, 1/v} in a column: the ray crosses the z
+// plane with centred coordinate kc at s = fma(kc, inv, off).
+struct ZLine {
+    float inv, off;
+};
+
+__device__ __forceinline__ ZLine z_line(float2 vr, float kE, float KD)
 {
-    LaneRay r;
-    r.zE = v * cp.kE;
-    r.inv_mz = cp.KD * rv;
-    r.sec = ray_sec(v, cp.invD);
-    r.stepz = (v >= 0.f) ? 1 : -1;
-    return r;
+    ZLine z;
+    z.inv = KD * vr.y;
+    z.off = -(vr.x * kE) * z.inv;
+    return z;
 }
 
-// s at which the ray leaves voxel layer iz in its direction of travel
-__device__ __forceinline__ float z_exit(int iz, const LaneRay &r, float halfnz)
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    const float kc = (float)(iz + (r.stepz > 0)) - halfnz;  // centred plane coordinate
-    return (kc - r.zE) * r.inv_mz;
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ void decode_block(const ProjGeom &G, int &j, int &iu, int &iv)
@@ -83,29 +83,10 @@ __device__ __forceinline__ void decode_block(const ProjGeom &G, int &j, int &iu,
     iv = rg * 32 + (threadIdx.x & 31);
 }
 
-// Per-lane state of the z part of the walk.
-struct ZWalk {
-    int iz;       // current voxel layer
-    float szn;    // xy distance at which the ray leaves layer iz
-    bool act;     // still inside the volume's z range
-};
-
-__device__ __forceinline__ ZWalk z_start(const LaneRay &r, bool ray_ok, const ProjGeom &G)
-{
-    ZWalk w;
-    w.iz = __float2int_rd(r.zE + G.halfnz);
-    w.act = ray_ok && w.iz >= 0 && w.iz < G.nz;
-    // the FP32 layer index can disagree with the sign of a tiny z offset: a
-    // first crossing "behind" the entry is taken at the entry
-    w.szn = fmaxf(z_exit(w.iz, r, G.halfnz), 0.f);
-    return w;
-}
-
 template <int MODE, bool NORM>
 __global__ void __launch_bounds__(256)
-fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *__restrict__ vrow,
-           const float *__restrict__ rvrow, const float *__restrict__ cells,
-           const float *__restrict__ vol,
+fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
+           const int4 *__restrict__ cells, const float *__restrict__ vol,
            float *__restrict__ out, const float *__restrict__ b, double *__restrict__ partials,
            int *__restrict__ nonfinite)
 {
@@ -118,40 +99,44 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *__restri
     if (col_ok) {
         const ColParams cp = cols[(long long)j * G.nu + iu];
         if (cp.ncells > 0) {
-            const float v = ray_ok ? __ldg(vrow + iv) : 0.f;
-            const float rv = ray_ok ? __ldg(rvrow + iv) : 1e30f;
-            const LaneRay r = lane_ray(cp, v, rv);
-            sec = r.sec;
-            ZWalk z = z_start(r, ray_ok, G);
-            if (__any_sync(kFull, z.act)) {
-                const float4 *t4 = reinterpret_cast<const float4 *>(cells) + cp.start4;
-                const int n = cp.ncells;
-                const int dcx = cp.stepx * G.ny * G.nz, dcy = cp.stepy * G.nz;
-                int colbase = (cp.ix0 * G.ny + cp.iy0) * G.nz;
+            const float2 w = ray_ok ? __ldg(vr + iv) : make_float2(0.f, 1e30f);
+            const ZLine zl = z_line(w, cp.kE, cp.KD);
+            sec = ray_sec(w.x, cp.invD);
+            const bool up = w.x >= 0.f;
+            const int stepz = up ? 1 : -1;
+            const float stepf = up ? 1.f : -1.f;
+            int iz = __float2int_rd(w.x * cp.kE + G.halfnz);
+            bool act = ray_ok && iz >= 0 && iz < G.nz;
+            if (!act) iz = 0;
+            // centred coordinate of the plane the ray leaves layer iz through
+            float kce = (float)(iz + (up ? 1 : 0)) - G.halfnz;
+            // the FP32 layer index can disagree with the sign of a tiny z
+            // offset: a first crossing "behind" the entry is taken at the entry
+            float szn = fmaxf(fmaf(kce, zl.inv, zl.off), 0.f);
+            if (__any_sync(kFull, act)) {
+                const int4 *t = cells + cp.start2;
+                const int n2 = (cp.ncells + 1) >> 1;
                 float s = 0.f;
-                // one xy cell [s, |e|]: the pieces of this lane's ray in it
-                auto cell = [&](float e) {
-                    const float se = fabsf(e);
-                    if (z.act) {
-                        acc = fmaf(fminf(z.szn, se) - s, __ldg(vol + colbase + z.iz), acc);
-                        while (z.szn < se) {
-                            const float sl = z.szn;
-                            z.iz += r.stepz;
-                            if ((unsigned)z.iz >= (unsigned)G.nz) { z.act = false; break; }
-                            z.szn = z_exit(z.iz, r, G.halfnz);
-                            acc = fmaf(fminf(z.szn, se) - sl, __ldg(vol + colbase + z.iz), acc);
+                // one xy cell [s, se] of voxel column colbase: this ray's pieces
+                auto cell = [&](int colbase, float se) {
+                    if (act) {
+                        acc = fmaf(fminf(szn, se) - s, __ldg(vol + colbase + iz), acc);
+                        while (szn < se) {
+                            const float sl = szn;
+                            iz += stepz;
+                            if ((unsigned)iz >= (unsigned)G.nz) { act = false; break; }
+                            kce += stepf;
+                            szn = fmaf(kce, zl.inv, zl.off);
+                            acc = fmaf(fminf(szn, se) - sl, __ldg(vol + colbase + iz), acc);
                         }
                     }
                     s = se;
-                    colbase += (__float_as_int(e) < 0) ? dcy : dcx;
                 };
-                for (int c = 0; c < n; c += 4) {
-                    const float4 e4 = __ldg(t4 + (c >> 2));
-                    cell(e4.x);
-                    if (c + 1 < n) cell(e4.y);
-                    if (c + 2 < n) cell(e4.z);
-                    if (c + 3 < n) cell(e4.w);
-                    if (!__any_sync(kFull, z.act)) break;
+                for (int c = 0; c < n2; ++c) {
+                    const int4 e = __ldg(t + c);
+                    cell(e.x, __int_as_float(e.y));
+                    cell(e.z, __int_as_float(e.w));
+                    if ((c & 1) && !__any_sync(kFull, act)) break;
                 }
             }
         }
@@ -188,7 +173,7 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *__restri
 
 // rs = proj * sec, per ray (the adjoint's gather then needs no square root)
 __global__ void __launch_bounds__(256)
-scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *__restrict__ vrow,
+scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const float *__restrict__ proj, float *__restrict__ rs)
 {
     int j, iu, iv;
@@ -196,56 +181,70 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *_
     if (iu >= G.nu || iv >= G.nv) return;
     const float invD = cols[(long long)j * G.nu + iu].invD;
     const long long idx = (long long)j * G.sj + (long long)iu * G.su + (long long)iv * G.sv;
-    rs[idx] = proj[idx] * ray_sec(__ldg(vrow + iv), invD);
+    rs[idx] = proj[idx] * ray_sec(__ldg(vr + iv).x, invD);
 }
 
 // Adjoint gather: CTA = one xy voxel column (ix, iy) and up to 256 z layers,
-// thread = one voxel.  For every crossing (view j, detector column iu, xy
-// interval [sa, sb]) of the voxel column, the rows whose rays pass through
-// layer k within [sa, sb] form a short interval of v (ray height z = v*G(s),
-// G(s) = kE + s*rKD); each is checked with the exact piece length.
-__global__ void __launch_bounds__(256)
-adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float *__restrict__ vrow,
-                  const float *__restrict__ rvrow, const int *__restrict__ hit_ptr,
-                  const CellHit *__restrict__ hits, const float *__restrict__ rs,
-                  float *__restrict__ vol)
+// thread = kLayersPerThread layers (k, k + 64, ...).  For every crossing
+// (view j, detector column iu, xy interval [sa, sb]) of the voxel column, the
+// rows whose rays pass through layer k inside [sa, sb] form a short interval
+// of heights v (ray z = v * G(s), G(s) = kE + s * rKD, so v in
+// [zl / G, zh / G]); each candidate row is checked with the exact piece
+// length, the same expression the forward walk evaluates.
+__global__ void __launch_bounds__(kGatherThreads)
+adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
+                  const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
+                  const float *__restrict__ rs, float *__restrict__ vol)
 {
+    constexpr int L = kLayersPerThread;
     const int cell = blockIdx.x;
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool kok = k < G.nz;
-    const float zl = (float)k - G.halfnz;  // centred coordinate of the layer's lower plane
-    const float zh = zl + 1.f;
+    const int kb = blockIdx.y * kGatherThreads * L + threadIdx.x;
+    float zlo[L], acc[L];
+    bool kok[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        const int k = kb + q * kGatherThreads;
+        kok[q] = k < G.nz;
+        zlo[q] = (float)k - G.halfnz;  // centred coordinate of the layer's lower plane
+        acc[q] = 0.f;
+    }
     const int h0 = __ldg(hit_ptr + cell), h1 = __ldg(hit_ptr + cell + 1);
-    float acc = 0.f;
     for (int h = h0; h < h1; ++h) {
         const CellHit e = __ldg(hits + h);
         const int j = e.x >> 16, iu = e.x & 0xffff;
         const float sa = __int_as_float(e.y), sb = __int_as_float(e.z);
         const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 2);
         const float kE = cz.x, KD = cz.y, rKD = cz.w;
-        // rays with z in [zl, zh] somewhere in [sa, sb]: v in [vlo, vhi]
-        const float rGa = __frcp_rn(fmaf(sa, rKD, kE)), rGb = __frcp_rn(fmaf(sb, rKD, kE));
-        const float vlo = fminf(zl * rGa, zl * rGb), vhi = fmaxf(zh * rGa, zh * rGb);
-        int ilo = (int)ceilf(fmaf(vlo, G.rdv, G.cv) - 1e-3f);
-        int ihi = (int)floorf(fmaf(vhi, G.rdv, G.cv) + 1e-3f);
-        ilo = max(ilo, 0);
-        ihi = kok ? min(ihi, G.nv - 1) : -1;
-        const long long rbase = (long long)j * G.sj + (long long)iu * G.su;
-        for (int iv = ilo; iv <= ihi; ++iv) {
-            const float v = __ldg(vrow + iv), rv = __ldg(rvrow + iv);
-            const float zE = v * kE, inv = KD * rv;
-            const bool up = v >= 0.f;
-            // plane the ray leaves layer k through, and the one it enters through
-            const float sx = ((up ? zh : zl) - zE) * inv;
-            const float sn = ((up ? zl : zh) - zE) * inv;
-            const float len = fminf(sb, sx) - fmaxf(sa, sn);
-            if (len > 0.f) acc = fmaf(len, __ldg(rs + rbase + (long long)iv * G.sv), acc);
+        // candidate bounds only: the rows are then checked exactly
+        const float rGa = rcp_approx(fmaf(sa, rKD, kE)), rGb = rcp_approx(fmaf(sb, rKD, kE));
+        const float *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const float zl = zlo[q], zh = zl + 1.f;
+            const float vlo = fminf(zl * rGa, zl * rGb), vhi = fmaxf(zh * rGa, zh * rGb);
+            int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
+            int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
+            ilo = max(ilo, 0);
+            ihi = kok[q] ? min(ihi, G.nv - 1) : -1;
+            auto cand = [&](int iv) {
+                const float2 w = __ldg(vr + iv);
+                const ZLine z = z_line(w, kE, KD);
+                const float xl = fmaf(zl, z.inv, z.off), xh = fmaf(zh, z.inv, z.off);
+                const bool up = w.x >= 0.f;
+                // enter through the lower plane and leave through the upper when
+                // going up, the other way round when going down
+                const float len = fminf(sb, up ? xh : xl) - fmaxf(sa, up ? xl : xh);
+                if (len > 0.f) acc[q] = fmaf(len, __ldg(rsc + (long long)iv * G.sv), acc[q]);
+            };
+            if (ilo <= ihi) cand(ilo);
+            if (ilo + 1 <= ihi) cand(ilo + 1);
+            if (ilo + 2 <= ihi) cand(ilo + 2);
+            for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
         }
     }
-    if (kok) {
-        const long long i = (long long)cell * G.nz + k;
-        vol[i] += acc;
-    }
+#pragma unroll
+    for (int q = 0; q < L; ++q)
+        if (kok[q]) vol[(long long)cell * G.nz + kb + q * kGatherThreads] += acc[q];
 }
 
 }  // namespace
@@ -257,40 +256,40 @@ int project_blocks(const ProjGeom &g)
     return ncg * nrg * g.n_views;
 }
 
-cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *rvrow, const float *cells, const float *vol, float *out,
-                           int mode, const float *b, double *partials, int *nonfinite,
-                           cudaStream_t st)
+cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                           const int4 *cells, const float *vol, float *out, int mode,
+                           const float *b, double *partials, int *nonfinite, cudaStream_t st)
 {
     const int nb = project_blocks(g);
     if (nb <= 0) return cudaSuccess;
     if (mode == FWD_RESID) {
         if (partials)
-            fwd_kernel<FWD_RESID, true><<<nb, 256, 0, st>>>(g, cols, vrow, rvrow, cells, vol, out, b, partials,
-                                                            nonfinite);
+            fwd_kernel<FWD_RESID, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
+                                                            partials, nonfinite);
         else
-            fwd_kernel<FWD_RESID, false><<<nb, 256, 0, st>>>(g, cols, vrow, rvrow, cells, vol, out, b, partials,
-                                                             nonfinite);
+            fwd_kernel<FWD_RESID, false><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
+                                                             partials, nonfinite);
     } else {
         if (partials)
-            fwd_kernel<FWD_PLAIN, true><<<nb, 256, 0, st>>>(g, cols, vrow, rvrow, cells, vol, out, b, partials,
-                                                            nonfinite);
+            fwd_kernel<FWD_PLAIN, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
+                                                            partials, nonfinite);
         else
-            fwd_kernel<FWD_PLAIN, false><<<nb, 256, 0, st>>>(g, cols, vrow, rvrow, cells, vol, out, b, partials,
-                                                             nonfinite);
+            fwd_kernel<FWD_PLAIN, false><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
+                                                             partials, nonfinite);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float *vrow,
-                           const float *rvrow, const int *hit_ptr, const CellHit *hits,
-                           const float *proj, float *rs, float *vol, cudaStream_t st)
+cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                           const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
+                           float *vol, cudaStream_t st)
 {
     const int nb = project_blocks(g);
     if (nb <= 0) return cudaSuccess;
-    scale_rays_kernel<<<nb, 256, 0, st>>>(g, cols, vrow, proj, rs);
-    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((g.nz + 255) / 256));
-    adj_gather_kernel<<<grid, 256, 0, st>>>(g, cols, vrow, rvrow, hit_ptr, hits, rs, vol);
+    scale_rays_kernel<<<nb, 256, 0, st>>>(g, cols, vr, proj, rs);
+    const int per_cta = kGatherThreads * kLayersPerThread;
+    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((g.nz + per_cta - 1) / per_cta));
+    adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol);
     return cudaGetLastError();
 }
 

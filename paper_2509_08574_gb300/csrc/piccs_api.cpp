@@ -36,8 +36,8 @@ struct piccs_ctx {
     void *base = nullptr;
     size_t bytes = 0;
     ColParams *cols = nullptr;
-    float *vrow = nullptr, *rvrow = nullptr;
-    float *cells = nullptr;
+    float2 *vr = nullptr;
+    int4 *cells = nullptr;
     int *hit_ptr = nullptr;
     CellHit *hits = nullptr;
     float *xprior = nullptr, *x = nullptr, *p = nullptr, *s = nullptr, *g = nullptr,
@@ -172,7 +172,7 @@ int check_params(const piccs_params *p, char *why, size_t n)
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t off_cols, off_vrow, off_rvrow, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
+    size_t off_cols, off_vr, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
         off_b, off_rs, off_pf, off_pv, off_pvec, off_ks,
         off_flag, off_dsum, total;
     int n_pf, n_pv, n_pvec;
@@ -190,9 +190,8 @@ Layout plan(const piccs_geometry *g)
     L.n_pvec = vector_blocks();
     size_t o = 0;
     L.off_cols = o; o += align256((size_t)g->n_views * g->nu * sizeof(ColParams));
-    L.off_vrow = o; o += align256((size_t)g->nv * sizeof(float));
-    L.off_rvrow = o; o += align256((size_t)g->nv * sizeof(float));
-    L.off_cells = o; o += align256((size_t)g->n_views * g->nu * cell_stride(g) * sizeof(float));
+    L.off_vr = o; o += align256((size_t)g->nv * sizeof(float2));
+    L.off_cells = o; o += align256((size_t)g->n_views * g->nu * cell_stride(g) * 2 * sizeof(int));
     L.off_hitptr = o; o += align256(((size_t)g->nx * g->ny + 1) * sizeof(int));
     L.off_hits = o; o += align256(hit_bound(g) * sizeof(CellHit));
     for (int i = 0; i < 9; ++i) { L.off_img[i] = o; o += align256(M * sizeof(float)); }
@@ -289,9 +288,8 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->bytes = L.total;
     char *b = static_cast<char *>(ctx->base);
     ctx->cols = reinterpret_cast<ColParams *>(b + L.off_cols);
-    ctx->vrow = reinterpret_cast<float *>(b + L.off_vrow);
-    ctx->rvrow = reinterpret_cast<float *>(b + L.off_rvrow);
-    ctx->cells = reinterpret_cast<float *>(b + L.off_cells);
+    ctx->vr = reinterpret_cast<float2 *>(b + L.off_vr);
+    ctx->cells = reinterpret_cast<int4 *>(b + L.off_cells);
     ctx->hit_ptr = reinterpret_cast<int *>(b + L.off_hitptr);
     ctx->hits = reinterpret_cast<CellHit *>(b + L.off_hits);
     float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
@@ -312,17 +310,15 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->dsum = reinterpret_cast<double *>(b + L.off_dsum);
 
     std::vector<ColParams> cols;
-    std::vector<float> vrow, rvrow, cells;
-    std::vector<int> hit_ptr;
+    std::vector<float2> vr;
+    std::vector<int> cells, hit_ptr;
     std::vector<CellHit> hits;
-    build_tables(&g, cols, vrow, rvrow, cells, hit_ptr, hits);
+    build_tables(&g, cols, vr, cells, hit_ptr, hits);
     e = cudaMemcpy(ctx->cols, cols.data(), cols.size() * sizeof(ColParams), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->vrow, vrow.data(), vrow.size() * sizeof(float), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->vr, vr.data(), vr.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->rvrow, rvrow.data(), rvrow.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->cells, cells.data(), cells.size() * sizeof(float), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->hit_ptr, hit_ptr.data(), hit_ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hits.empty())
@@ -417,7 +413,7 @@ int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, d_vol, d_proj, FWD_PLAIN, nullptr,
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, d_vol, d_proj, FWD_PLAIN, nullptr,
                                  nullptr, nullptr, ctx->stream));
     return PICCS_OK;
 }
@@ -427,7 +423,7 @@ int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol)
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
     CUDA_TRY(ctx, cudaMemsetAsync(d_vol, 0, ctx->M * sizeof(float), ctx->stream));
-    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, d_proj, ctx->rs, d_vol, ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, d_proj, ctx->rs, d_vol, ctx->stream));
     return PICCS_OK;
 }
 
@@ -501,7 +497,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, d_x0, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,
                                  nullptr, &ctx->ks->nonfinite, st));
     for (int k = 0; k < p->n_outer; ++k) {
         // reweighting at the previous iterate (Eqs. 10-11)
@@ -511,7 +507,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         if (k == 0) {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
                                              ctx->s, 1, nullptr, st));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st));
         } else {
@@ -522,13 +518,13 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         for (int it = 0; it < p->n_inner; ++it) {
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st));
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st));
-            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->cells, ctx->p, ctx->q, FWD_PLAIN,
+            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p, ctx->q, FWD_PLAIN,
                                          nullptr, ctx->part_fwd, nullptr, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
                                                 ctx->part_vol, ctx->n_part_vol, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
                                           ctx->q, ctx->ks, st));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vrow, ctx->rvrow, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st));
         }

@@ -3,11 +3,10 @@
 //
 // For every (view, detector column) the xy part of the Siddon walk is the same
 // for all rows of the column, so it is walked once here, in FP64, and stored as
-// the list of xy cells the column's rays cross: per cell the xy distance (mm,
-// measured from the entry into the volume's xy square) at which the rays leave
-// it, rounded once to FP32, with the sign bit set when the next cell is reached
-// by a step in y (clear: a step in x).  The kernels then only add the z
-// crossings, per row, in FP32.
+// the list of xy cells the column's rays cross: per cell the flat index of its
+// first voxel and the xy distance (mm, measured from the entry into the
+// volume's xy square) at which the rays leave it, rounded once to FP32.  The
+// kernels then only add the z crossings, per row, in FP32.
 #pragma once
 
 #include <algorithm>
@@ -21,13 +20,14 @@
 
 namespace piccs {
 
-// Floats reserved per column: a column crosses at most nx + ny - 1 cells;
-// rounded up to whole float4 loads.
-inline int cell_stride(const piccs_geometry *g) { return ((g->nx + g->ny + 3) / 4) * 4; }
+// Cells reserved per column: a column crosses at most nx + ny - 1 cells;
+// rounded up to an even count (two cells per 16-byte load).
+inline int cell_stride(const piccs_geometry *g) { return ((g->nx + g->ny + 1) / 2) * 2; }
 
-// Walks one column in FP64; fills cp (start cell, steps, z constants) and the
-// column's cell list; returns the number of cells.
-inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, float *cells)
+// Walks one column in FP64; fills cp (z constants, cell count) and the
+// column's cell list (two ints per cell: first voxel index, exit distance
+// bits), padded to an even count; returns the number of cells.
+inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, int *cells)
 {
     const double Wx = g->nx * g->vx, Wy = g->ny * g->vy;
     const double cth = std::cos(g->angles_rad[j]), sth = std::sin(g->angles_rad[j]);
@@ -68,10 +68,6 @@ inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, fl
     auto next_y = [&](int i) {
         return cy != 0.0 ? std::max(((i + (sty > 0)) - ey) * invy, 0.0) : INFINITY;
     };
-    cp.ix0 = ix;
-    cp.iy0 = iy;
-    cp.stepx = stx;
-    cp.stepy = sty;
     cp.kE = (float)(s0 / (D * g->vz));
     cp.KD = (float)(g->vz * D);
     cp.invD = (float)(1.0 / D);
@@ -84,9 +80,10 @@ inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, fl
         const bool xstep = sxn <= syn;
         if (!last) last = xstep ? (unsigned)(ix + stx) >= (unsigned)g->nx
                                 : (unsigned)(iy + sty) >= (unsigned)g->ny;
-        float e = (float)se;
-        if (!last && !xstep) e = -e;  // sign bit: the next cell is one step in y
-        cells[n++] = e;
+        const float e = (float)se;
+        cells[2 * n] = (ix * g->ny + iy) * g->nz;
+        std::memcpy(&cells[2 * n + 1], &e, 4);
+        ++n;
         if (last) break;
         if (xstep) {
             ix += stx;
@@ -97,29 +94,31 @@ inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, fl
         }
     }
     cp.ncells = n;
+    if (n & 1) {  // pad: a zero-length copy of the last cell
+        cells[2 * n] = cells[2 * n - 2];
+        cells[2 * n + 1] = cells[2 * n - 1];
+    }
     return n;
 }
 
-// Per (view, column) constants, per-row detector heights v and 1/v, the cell
-// table (cell_stride floats per column, column (j, iu) at offset
+// Per (view, column) constants, per-row {v, 1/v} (1e30 for v = 0), the cell
+// table (cell_stride cells per column, column (j, iu) at cell offset
 // (j*nu + iu)*stride) and its transpose: for every xy voxel column
 // (ix*ny + iy) the crossings hits[hit_ptr[c] .. hit_ptr[c+1]) by detector
 // columns, in view-then-column order.
 inline void build_tables(const piccs_geometry *g, std::vector<ColParams> &cols,
-                         std::vector<float> &vrow, std::vector<float> &rvrow,
-                         std::vector<float> &cells, std::vector<int> &hit_ptr,
-                         std::vector<CellHit> &hits)
+                         std::vector<float2> &vr, std::vector<int> &cells,
+                         std::vector<int> &hit_ptr, std::vector<CellHit> &hits)
 {
     const size_t ncol = (size_t)g->n_views * g->nu;
     const int stride = cell_stride(g);
     cols.assign(ncol, ColParams{});
-    cells.assign(ncol * (size_t)stride, 0.f);
-    vrow.resize(g->nv);
-    rvrow.resize(g->nv);
+    cells.assign(ncol * (size_t)stride * 2, 0);
+    vr.resize(g->nv);
     for (int iv = 0; iv < g->nv; ++iv) {
         const double v = (iv - 0.5 * (g->nv - 1)) * g->dv;
-        vrow[iv] = (float)v;
-        rvrow[iv] = v != 0.0 ? (float)(1.0 / v) : 1e30f;
+        vr[iv].x = (float)v;
+        vr[iv].y = v != 0.0 ? (float)(1.0 / v) : 1e30f;
     }
     unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     nt = (unsigned)std::min<size_t>(nt, (size_t)g->n_views);
@@ -129,8 +128,8 @@ inline void build_tables(const piccs_geometry *g, std::vector<ColParams> &cols,
             for (int j = (int)t; j < g->n_views; j += (int)nt)
                 for (int iu = 0; iu < g->nu; ++iu) {
                     const size_t c = (size_t)j * g->nu + iu;
-                    walk_column(g, j, iu, cols[c], cells.data() + c * stride);
-                    cols[c].start4 = (long long)(c * stride / 4);
+                    walk_column(g, j, iu, cols[c], cells.data() + c * stride * 2);
+                    cols[c].start2 = (long long)(c * stride / 2);
                 }
         });
     }
@@ -141,15 +140,13 @@ inline void build_tables(const piccs_geometry *g, std::vector<ColParams> &cols,
     hit_ptr.assign(nxy + 1, 0);
     auto for_each_cell = [&](auto &&fn) {
         for (size_t c = 0; c < ncol; ++c) {
-            const ColParams &cp = cols[c];
-            const float *e = cells.data() + c * stride;
-            int ix = cp.ix0, iy = cp.iy0;
+            const int *e = cells.data() + c * stride * 2;
             float sa = 0.f;
-            for (int k = 0; k < cp.ncells; ++k) {
-                fn(c, (size_t)ix * g->ny + iy, sa, std::fabs(e[k]));
-                sa = std::fabs(e[k]);
-                if (std::signbit(e[k])) iy += cp.stepy;
-                else ix += cp.stepx;
+            for (int k = 0; k < cols[c].ncells; ++k) {
+                float sb;
+                std::memcpy(&sb, &e[2 * k + 1], 4);
+                fn(c, (size_t)(e[2 * k] / g->nz), sa, sb);
+                sa = sb;
             }
         }
     };

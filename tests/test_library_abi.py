@@ -78,8 +78,8 @@ def test_workspace_size(pk):
     b = pk.piccs_query_workspace(g)
     M, N = g.M, g.N
     ncol = g.n_views * g.nu
-    stride = (g.nx + g.ny + 3) // 4 * 4
-    # nine image vectors, four data vectors, the column cell table (4 B per cell
+    stride = (g.nx + g.ny + 1) // 2 * 2
+    # nine image vectors, four data vectors, the column cell table (8 B per cell
     # slot) and its transpose (16 B per crossing, bounded by nx + ny - 1 per column)
-    expect = 4 * (9 * M + 4 * N) + 4 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
+    expect = 4 * (9 * M + 4 * N) + 8 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
     assert expect <= b <= expect + (16 << 20)
