@@ -94,8 +94,48 @@ def traffic_record(kernel):
         return None
     if rec.get("source_sha256") != h:
         return None
-    ent = rec.get("kernels", {}).get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    total = 0.0
+    for name in kernel.split("+"):
+        ent = rec.get("kernels", {}).get(name)
+        if ent is None:
+            return None
+        total += float(ent["dram_bytes_per_launch"])
+    return total
+
+
+def parse_clock_csv(text):
+    """Median SM clock, max clock and the throttle reasons seen, from the
+    nvidia-smi CSV lines the sampler wrote (fields as ClockSampler.FIELDS)."""
+    rows = []
+    for line in text.splitlines():
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                      if v.lower().startswith("active")})
+    return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows)}
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of floats over all ranks (identity
+    without an initialised process group); device is where the collective's
+    tensor lives (cuda for NCCL, cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
 
 
 class ClockSampler:
@@ -135,24 +175,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-                except ValueError:
-                    continue
+            text = f.read()
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
-                          if v.lower().startswith("active")})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return parse_clock_csv(text)
 
 
 def pctl(xs, q):
@@ -290,10 +316,7 @@ def run_ours(args):
     p50, p99 = pctl(step_ms, 50), pctl(step_ms, 99)
     total_ms = float(sum(step_ms))
 
-    if world > 1:
-        t = torch.tensor([p50, p99, total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p50, p99, total_ms = (float(v) for v in t.tolist())
+    p50, p99, total_ms = max_over_ranks([p50, p99, total_ms], "cuda")
 
     # end to end through the public API with host buffers (copies inside)
     hb = torch.from_numpy(b_np).pin_memory()
@@ -309,11 +332,7 @@ def run_ours(args):
         dt = (time.perf_counter() - t0) * 1e3
         if k > 0:  # first call warms the pinned-memory path
             e2e_ms.append(dt)
-    e2e_p50 = pctl(e2e_ms, 50)
-    if world > 1:
-        t = torch.tensor([e2e_p50], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_p50 = float(t.item())
+    e2e_p50 = max_over_ranks([pctl(e2e_ms, 50)], "cuda")[0]
 
     # roofline of the dominant kernel (measured live inside the timed region)
     nnz = nnz_of(scan)
@@ -326,7 +345,7 @@ def run_ours(args):
     alg_bytes = 4.0 * (nnz + g.M + g.N)
     achieved = alg_bytes / (per[dom] * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    kernel_names = {"forward": "fwd_kernel", "adjoint": "adj_kernel"}
+    kernel_names = {"forward": "fwd_kernel", "adjoint": "scale_rays_kernel+adj_gather_kernel"}
 
     line = {
         "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
