@@ -18,15 +18,15 @@ namespace piccs {
 // column's entry into the volume's xy square) at which the rays leave it.  An
 // odd list is padded with a zero-length copy of its last cell.
 // Row v (detector height, mm, with rv = 1/v, or 1e30 for v = 0) has z (voxel
-// units, centred) = v * (kE + s * rKD); with inv = KD * rv and
-// off = -(v * kE) * inv it crosses the z plane with centred coordinate kc at
-// s = fma(kc, inv, off), and its 3D length per unit s is sqrt(1 + (v*invD)^2).
+// units, centred) = v * (s0 + s) * rKD, so it crosses the z plane with
+// centred coordinate kc at s = kc * (KD * rv) - s0, evaluated as
+// fma(kc, KD * rv, -s0); s0 is the xy distance from the source to the
+// column's entry point.  Its 3D length per unit s is sqrt(1 + (v * invD)^2).
 struct __align__(16) ColParams {
     long long start2;        // int4 index of the column's first pair of cells
     int ncells;              // 0: the column misses the volume
     int pad0;
-    int pad1, pad2, pad3, pad4;
-    float kE, KD, invD, rKD; // one 16-byte load for the adjoint's gather
+    float s0, KD, invD, rKD; // one 16-byte load for the adjoint's gather
 };
 
 // One crossing of an xy voxel column by a detector column (the transpose of
@@ -41,6 +41,7 @@ struct ProjGeom {
     long long sj, su, sv;   // projection strides of view, column, row
     float halfnz;           // nz / 2
     float rdv, cv;          // 1 / dv and (nv - 1) / 2: row index of height v = v * rdv + cv
+    int sv32;               // sv as a 32-bit stride (1 or nu)
 };
 
 // Device-side Krylov scalars (FP64), read by every vector kernel so that no

@@ -7,7 +7,8 @@
 // of the bytes of a reconstruction.
 //
 // Layout of the work: one warp = 32 consecutive detector rows of one detector
-// column of one view; one CTA = 8 adjacent columns.  Because the detector v
+// column of one view; one CTA = 8 such warps of the same column (256 rows),
+// so the column's cell list is fetched from DRAM once per CTA.  Because the detector v
 // axis is parallel to the rotation axis and the source lies in z = 0, every
 // ray of a column has the same xy path.  That path is walked once per
 // geometry on the host (FP64, ray_tables.h) and stored as the column's cell
@@ -25,9 +26,9 @@
 // voxel, deterministic.  Both kernels evaluate the same piece lengths
 //   len = min(s_exit_xy, s_z(exit plane)) - max(s_enter_xy, s_z(entry plane))
 // from the same FP32 cell boundaries and the same plane-crossing formula
-// fma(kc, inv, off), with the exact plane coordinate kc (never an accumulated
-// distance), so A^T applies bit-identical weights to A; only the order of the
-// FP32 sums differs.
+// fma(kc, KD / v, -s0), with the exact plane coordinate kc (never an
+// accumulated distance), so A^T applies bit-identical weights to A; only the
+// order of the FP32 sums differs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,7 +39,7 @@ namespace piccs {
 
 namespace {
 
-constexpr int kWarps = 8;        // detector columns per CTA (forward)
+constexpr int kRowGroups = 8;    // warps per forward CTA: 8 x 32 rows of one column
 constexpr int kGatherThreads = 64;
 constexpr int kLayersPerThread = 4;
 constexpr unsigned kFull = 0xffffffffu;
@@ -50,20 +51,6 @@ __device__ __forceinline__ float ray_sec(float v, float invD)
     return __fsqrt_rn(fmaf(m, m, 1.f));
 }
 
-// z-crossing constants of row {v, 1/v} in a column: the ray crosses the z
-// plane with centred coordinate kc at s = fma(kc, inv, off).
-struct ZLine {
-    float inv, off;
-};
-
-__device__ __forceinline__ ZLine z_line(float2 vr, float kE, float KD)
-{
-    ZLine z;
-    z.inv = KD * vr.y;
-    z.off = -(vr.x * kE) * z.inv;
-    return z;
-}
-
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -71,16 +58,13 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-__device__ __forceinline__ void decode_block(const ProjGeom &G, int &j, int &iu, int &iv)
+// CTA = one detector column (j, iu) and kRowGroups groups of 32 rows
+__device__ __forceinline__ void decode_block(const ProjGeom &G, int &col, int &iv)
 {
-    int b = blockIdx.x;
-    const int ncg = (G.nu + kWarps - 1) / kWarps;
-    const int cg = b % ncg;
-    b /= ncg;
-    j = b % G.n_views;
-    const int rg = b / G.n_views;
-    iu = cg * kWarps + (threadIdx.x >> 5);
-    iv = rg * 32 + (threadIdx.x & 31);
+    const int nrgb = (G.nv + 32 * kRowGroups - 1) / (32 * kRowGroups);
+    const int b = blockIdx.x;
+    col = b / nrgb;
+    iv = ((b - col * nrgb) * kRowGroups + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
 }
 
 template <int MODE, bool NORM>
@@ -90,60 +74,58 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
            float *__restrict__ out, const float *__restrict__ b, double *__restrict__ partials,
            int *__restrict__ nonfinite)
 {
-    int j, iu, iv;
-    decode_block(G, j, iu, iv);
-    const bool col_ok = iu < G.nu;
-    const bool ray_ok = col_ok && iv < G.nv;
+    int col, iv;
+    decode_block(G, col, iv);
+    const bool ray_ok = iv < G.nv;
     float acc = 0.f, sec = 1.f;
-
-    if (col_ok) {
-        const ColParams cp = cols[(long long)j * G.nu + iu];
-        if (cp.ncells > 0) {
-            const float2 w = ray_ok ? __ldg(vr + iv) : make_float2(0.f, 1e30f);
-            const ZLine zl = z_line(w, cp.kE, cp.KD);
-            sec = ray_sec(w.x, cp.invD);
-            const bool up = w.x >= 0.f;
-            const int stepz = up ? 1 : -1;
-            const float stepf = up ? 1.f : -1.f;
-            int iz = __float2int_rd(w.x * cp.kE + G.halfnz);
-            bool act = ray_ok && iz >= 0 && iz < G.nz;
-            if (!act) iz = 0;
-            // centred coordinate of the plane the ray leaves layer iz through
-            float kce = (float)(iz + (up ? 1 : 0)) - G.halfnz;
-            // the FP32 layer index can disagree with the sign of a tiny z
-            // offset: a first crossing "behind" the entry is taken at the entry
-            float szn = fmaxf(fmaf(kce, zl.inv, zl.off), 0.f);
-            if (__any_sync(kFull, act)) {
-                const int4 *t = cells + cp.start2;
-                const int n2 = (cp.ncells + 1) >> 1;
-                float s = 0.f;
-                // one xy cell [s, se] of voxel column colbase: this ray's pieces
-                auto cell = [&](int colbase, float se) {
-                    if (act) {
-                        acc = fmaf(fminf(szn, se) - s, __ldg(vol + colbase + iz), acc);
-                        while (szn < se) {
-                            const float sl = szn;
-                            iz += stepz;
-                            if ((unsigned)iz >= (unsigned)G.nz) { act = false; break; }
-                            kce += stepf;
-                            szn = fmaf(kce, zl.inv, zl.off);
-                            acc = fmaf(fminf(szn, se) - sl, __ldg(vol + colbase + iz), acc);
-                        }
+    const ColParams cp = cols[col];
+    if (cp.ncells > 0) {
+        const float2 w = ray_ok ? __ldg(vr + iv) : make_float2(0.f, 1e30f);
+        const float inv = cp.KD * w.y;  // xy distance per voxel of z (signed)
+        sec = ray_sec(w.x, cp.invD);
+        const bool up = w.y > 0.f;      // rv = 1e30 > 0 for v = 0
+        const int stepz = up ? 1 : -1;
+        const float stepf = up ? 1.f : -1.f;
+        int iz = __float2int_rd(w.x * (cp.s0 * cp.rKD) + G.halfnz);
+        bool act = ray_ok && iz >= 0 && iz < G.nz;
+        if (!act) iz = 0;
+        // centred coordinate of the plane the ray leaves layer iz through
+        float kce = (float)(iz + (up ? 1 : 0)) - G.halfnz;
+        // the FP32 layer index can disagree with the sign of a tiny z offset:
+        // a first crossing "behind" the entry is taken at the entry
+        float szn = fmaxf(fmaf(kce, inv, -cp.s0), 0.f);
+        if (__any_sync(kFull, act)) {
+            const int4 *t = cells + cp.start2;
+            const int n2 = (cp.ncells + 1) >> 1;
+            float s = 0.f;
+            // one xy cell [s, se] of the voxel column at colbase: this ray's pieces
+            auto cell = [&](int colbase, float se) {
+                const float *cpv = vol + colbase;
+                if (act) {
+                    acc = fmaf(fminf(szn, se) - s, __ldg(cpv + iz), acc);
+                    while (szn < se) {
+                        const float sl = szn;
+                        iz += stepz;
+                        if ((unsigned)iz >= (unsigned)G.nz) { act = false; break; }
+                        kce += stepf;
+                        szn = fmaf(kce, inv, -cp.s0);
+                        acc = fmaf(fminf(szn, se) - sl, __ldg(cpv + iz), acc);
                     }
-                    s = se;
-                };
-                for (int c = 0; c < n2; ++c) {
-                    const int4 e = __ldg(t + c);
-                    cell(e.x, __int_as_float(e.y));
-                    cell(e.z, __int_as_float(e.w));
-                    if ((c & 1) && !__any_sync(kFull, act)) break;
                 }
+                s = se;
+            };
+            for (int c = 0; c < n2; ++c) {
+                const int4 e = __ldg(t + c);
+                cell(e.x, __int_as_float(e.y));
+                cell(e.z, __int_as_float(e.w));
+                if ((c & 1) && !__any_sync(kFull, act)) break;
             }
         }
     }
 
     float val = 0.f;
     if (ray_ok) {
+        const int j = col / G.nu, iu = col - j * G.nu;
         const long long idx = (long long)j * G.sj + (long long)iu * G.su + (long long)iv * G.sv;
         const float q = sec * acc;
         if (MODE == FWD_RESID) {
@@ -156,7 +138,7 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         out[idx] = val;
     }
     if (NORM) {
-        __shared__ double red[kWarps];
+        __shared__ double red[kRowGroups];
         float sq = val * val;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
@@ -165,7 +147,7 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         if (threadIdx.x == 0) {
             double t = 0.0;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) t += red[w];
+            for (int w = 0; w < kRowGroups; ++w) t += red[w];
             partials[blockIdx.x] = t;
         }
     }
@@ -176,21 +158,21 @@ __global__ void __launch_bounds__(256)
 scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const float *__restrict__ proj, float *__restrict__ rs)
 {
-    int j, iu, iv;
-    decode_block(G, j, iu, iv);
-    if (iu >= G.nu || iv >= G.nv) return;
-    const float invD = cols[(long long)j * G.nu + iu].invD;
+    int col, iv;
+    decode_block(G, col, iv);
+    if (iv >= G.nv) return;
+    const int j = col / G.nu, iu = col - j * G.nu;
     const long long idx = (long long)j * G.sj + (long long)iu * G.su + (long long)iv * G.sv;
-    rs[idx] = proj[idx] * ray_sec(__ldg(vr + iv).x, invD);
+    rs[idx] = proj[idx] * ray_sec(__ldg(vr + iv).x, cols[col].invD);
 }
 
 // Adjoint gather: CTA = one xy voxel column (ix, iy) and up to 256 z layers,
 // thread = kLayersPerThread layers (k, k + 64, ...).  For every crossing
 // (view j, detector column iu, xy interval [sa, sb]) of the voxel column, the
 // rows whose rays pass through layer k inside [sa, sb] form a short interval
-// of heights v (ray z = v * G(s), G(s) = kE + s * rKD, so v in
-// [zl / G, zh / G]); each candidate row is checked with the exact piece
-// length, the same expression the forward walk evaluates.
+// of heights v (ray z = v * (s0 + s) * rKD, so v in [zl, zh] / ((s0 + s) rKD));
+// each candidate row is checked with the exact piece length, the same
+// expression the forward walk evaluates.
 __global__ void __launch_bounds__(kGatherThreads)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
@@ -213,10 +195,10 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
         const CellHit e = __ldg(hits + h);
         const int j = e.x >> 16, iu = e.x & 0xffff;
         const float sa = __int_as_float(e.y), sb = __int_as_float(e.z);
-        const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 2);
-        const float kE = cz.x, KD = cz.y, rKD = cz.w;
+        const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 1);
+        const float s0 = cz.x, KD = cz.y, rKD = cz.w;
         // candidate bounds only: the rows are then checked exactly
-        const float rGa = rcp_approx(fmaf(sa, rKD, kE)), rGb = rcp_approx(fmaf(sb, rKD, kE));
+        const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
         const float *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
 #pragma unroll
         for (int q = 0; q < L; ++q) {
@@ -227,14 +209,11 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             ilo = max(ilo, 0);
             ihi = kok[q] ? min(ihi, G.nv - 1) : -1;
             auto cand = [&](int iv) {
-                const float2 w = __ldg(vr + iv);
-                const ZLine z = z_line(w, kE, KD);
-                const float xl = fmaf(zl, z.inv, z.off), xh = fmaf(zh, z.inv, z.off);
-                const bool up = w.x >= 0.f;
-                // enter through the lower plane and leave through the upper when
-                // going up, the other way round when going down
-                const float len = fminf(sb, up ? xh : xl) - fmaxf(sa, up ? xl : xh);
-                if (len > 0.f) acc[q] = fmaf(len, __ldg(rsc + (long long)iv * G.sv), acc[q]);
+                const float inv = KD * __ldg(vr + iv).y;
+                const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
+                // the ray is inside the layer between its two plane crossings
+                const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
+                if (len > 0.f) acc[q] = fmaf(len, __ldg(rsc + iv * G.sv32), acc[q]);
             };
             if (ilo <= ihi) cand(ilo);
             if (ilo + 1 <= ihi) cand(ilo + 1);
@@ -251,9 +230,8 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 
 int project_blocks(const ProjGeom &g)
 {
-    const int ncg = (g.nu + kWarps - 1) / kWarps;
-    const int nrg = (g.nv + 31) / 32;
-    return ncg * nrg * g.n_views;
+    const int nrgb = (g.nv + 32 * kRowGroups - 1) / (32 * kRowGroups);
+    return g.n_views * g.nu * nrgb;
 }
 
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,

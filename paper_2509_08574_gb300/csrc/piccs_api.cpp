@@ -278,6 +278,7 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->pg.halfnz = 0.5f * (float)g.nz;
     ctx->pg.rdv = (float)(1.0 / g.dv);
     ctx->pg.cv = 0.5f * (float)(g.nv - 1);
+    ctx->pg.sv32 = (int)ctx->pg.sv;
     ctx->vd = VolDims{g.nx, g.ny, g.nz};
 
     e = cudaMalloc(&ctx->base, L.total);

@@ -68,7 +68,7 @@ inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, in
     auto next_y = [&](int i) {
         return cy != 0.0 ? std::max(((i + (sty > 0)) - ey) * invy, 0.0) : INFINITY;
     };
-    cp.kE = (float)(s0 / (D * g->vz));
+    cp.s0 = (float)s0;
     cp.KD = (float)(g->vz * D);
     cp.invD = (float)(1.0 / D);
     cp.rKD = (float)(1.0 / (g->vz * D));

@@ -151,7 +151,9 @@ def test_forward_c2_sampled_rays(pk, c2_volume):
     assert rel_l2(y[rays], ref) <= TOL
     hit = ref > 0
     assert hit.sum() > 1000
-    assert np.max(np.abs(y[rays] - ref) / np.maximum(ref, 1e-3)) < 1e-4
+    # per ray: FP32 ray coordinates carry ~1e-5 voxel of rounding, so a ray's
+    # error is bounded in absolute terms (grazing chords have tiny values)
+    assert np.max(np.abs(y[rays] - ref)) <= 1e-5 * np.abs(ref).max()
 
 
 @pytest.mark.slow
