@@ -39,9 +39,9 @@ namespace piccs {
 
 namespace {
 
-constexpr int kRowGroups = 8;    // warps per forward CTA: 8 x 32 rows of one column
+constexpr int kRowGroups = 8;    // warps per forward CTA: 8 x 32 row pairs of one column
 constexpr int kGatherThreads = 64;
-constexpr int kLayersPerThread = 4;
+constexpr int kLayersPerThread = 2;  // layer pairs per gather thread
 constexpr unsigned kFull = 0xffffffffu;
 
 // per-ray factor: 3D length per unit of xy length
@@ -58,13 +58,27 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// CTA = one detector column (j, iu) and kRowGroups groups of 32 rows
-__device__ __forceinline__ void decode_block(const ProjGeom &G, int &col, int &iv)
+// The geometry is symmetric about the plane z = 0 (source in it, detector and
+// volume centred on it): detector rows iv and nv-1-iv have heights v and -v
+// exactly (also in FP32), and their rays are mirror images.  With
+// s(kc) = fma(kc, KD/v, -s0), the ray at -v crosses plane -kc at the same s
+// as the ray at v crosses plane kc, bit for bit, and it is in layer nz-1-k
+// whenever the ray at v is in layer k.  Both kernels therefore work on
+// mirror pairs: the forward walks the pair with one shared z state, the
+// gather evaluates each piece length once for a layer and its mirror.
+
+// Rows of pair p: the upper row nv-1-p (v >= 0, walked upwards) and the lower
+// row p (its mirror; absent when both are the middle row of an odd nv).
+__device__ __forceinline__ int npairs_rows(int nv) { return (nv + 1) >> 1; }
+
+// CTA = one detector column (j, iu) and kRowGroups x 32 row pairs
+__device__ __forceinline__ void decode_block(const ProjGeom &G, int &col, int &p)
 {
-    const int nrgb = (G.nv + 32 * kRowGroups - 1) / (32 * kRowGroups);
+    const int np = npairs_rows(G.nv);
+    const int nrgb = (np + 32 * kRowGroups - 1) / (32 * kRowGroups);
     const int b = blockIdx.x;
     col = b / nrgb;
-    iv = ((b - col * nrgb) * kRowGroups + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
+    p = ((b - col * nrgb) * kRowGroups + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
 }
 
 template <int MODE, bool NORM>
@@ -74,23 +88,23 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
            float *__restrict__ out, const float *__restrict__ b, double *__restrict__ partials,
            int *__restrict__ nonfinite)
 {
-    int col, iv;
-    decode_block(G, col, iv);
-    const bool ray_ok = iv < G.nv;
-    float acc = 0.f, sec = 1.f;
+    int col, p;
+    decode_block(G, col, p);
+    const bool pair_ok = p < npairs_rows(G.nv);
+    const int iva = G.nv - 1 - p;               // upper row (v >= 0)
+    const bool has_b = pair_ok && p != iva;     // lower mirror row p
+    float acca = 0.f, accb = 0.f, sec = 1.f;
     const ColParams cp = cols[col];
     if (cp.ncells > 0) {
-        const float2 w = ray_ok ? __ldg(vr + iv) : make_float2(0.f, 1e30f);
-        const float inv = cp.KD * w.y;  // xy distance per voxel of z (signed)
+        const float2 w = pair_ok ? __ldg(vr + iva) : make_float2(0.f, 1e30f);
+        const float inv = cp.KD * w.y;          // xy distance per voxel of z (> 0)
         sec = ray_sec(w.x, cp.invD);
-        const bool up = w.y > 0.f;      // rv = 1e30 > 0 for v = 0
-        const int stepz = up ? 1 : -1;
-        const float stepf = up ? 1.f : -1.f;
+        const int nzm1 = G.nz - 1;
         int iz = __float2int_rd(w.x * (cp.s0 * cp.rKD) + G.halfnz);
-        bool act = ray_ok && iz >= 0 && iz < G.nz;
+        bool act = pair_ok && iz >= 0 && iz < G.nz;
         if (!act) iz = 0;
-        // centred coordinate of the plane the ray leaves layer iz through
-        float kce = (float)(iz + (up ? 1 : 0)) - G.halfnz;
+        // centred coordinate of the plane the upper ray leaves layer iz through
+        float kce = (float)(iz + 1) - G.halfnz;
         // the FP32 layer index can disagree with the sign of a tiny z offset:
         // a first crossing "behind" the entry is taken at the entry
         float szn = fmaxf(fmaf(kce, inv, -cp.s0), 0.f);
@@ -98,18 +112,21 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
             const int4 *t = cells + cp.start2;
             const int n2 = (cp.ncells + 1) >> 1;
             float s = 0.f;
-            // one xy cell [s, se] of the voxel column at colbase: this ray's pieces
+            // one xy cell [s, se] of the voxel column at colbase: the pair's pieces
             auto cell = [&](int colbase, float se) {
                 const float *cpv = vol + colbase;
                 if (act) {
-                    acc = fmaf(fminf(szn, se) - s, __ldg(cpv + iz), acc);
+                    float len = fminf(szn, se) - s;
+                    acca = fmaf(len, __ldg(cpv + iz), acca);
+                    accb = fmaf(len, __ldg(cpv + (nzm1 - iz)), accb);
                     while (szn < se) {
                         const float sl = szn;
-                        iz += stepz;
-                        if ((unsigned)iz >= (unsigned)G.nz) { act = false; break; }
-                        kce += stepf;
+                        if (++iz >= G.nz) { act = false; break; }
+                        kce += 1.f;
                         szn = fmaf(kce, inv, -cp.s0);
-                        acc = fmaf(fminf(szn, se) - sl, __ldg(cpv + iz), acc);
+                        len = fminf(szn, se) - sl;
+                        acca = fmaf(len, __ldg(cpv + iz), acca);
+                        accb = fmaf(len, __ldg(cpv + (nzm1 - iz)), accb);
                     }
                 }
                 s = se;
@@ -123,23 +140,25 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         }
     }
 
-    float val = 0.f;
-    if (ray_ok) {
+    float sq = 0.f;
+    if (pair_ok) {
         const int j = col / G.nu, iu = col - j * G.nu;
-        const long long idx = (long long)j * G.sj + (long long)iu * G.su + (long long)iv * G.sv;
-        const float q = sec * acc;
+        const long long base = (long long)j * G.sj + (long long)iu * G.su;
+        const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
+        float qa = sec * acca, qb = sec * accb;
         if (MODE == FWD_RESID) {
-            const float bb = b[idx];
-            if (!isfinite(bb)) atomicOr(nonfinite, 1);
-            val = bb - q;
-        } else {
-            val = q;
+            const float ba = b[ia];
+            const float bb = has_b ? b[ib] : 0.f;
+            if (!isfinite(ba) || !isfinite(bb)) atomicOr(nonfinite, 1);
+            qa = ba - qa;
+            qb = bb - qb;
         }
-        out[idx] = val;
+        out[ia] = qa;
+        if (has_b) out[ib] = qb;
+        sq = qa * qa + (has_b ? qb * qb : 0.f);
     }
     if (NORM) {
         __shared__ double red[kRowGroups];
-        float sq = val * val;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)sq;
@@ -158,21 +177,26 @@ __global__ void __launch_bounds__(256)
 scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const float *__restrict__ proj, float *__restrict__ rs)
 {
-    int col, iv;
-    decode_block(G, col, iv);
-    if (iv >= G.nv) return;
+    int col, p;
+    decode_block(G, col, p);
+    if (p >= npairs_rows(G.nv)) return;
     const int j = col / G.nu, iu = col - j * G.nu;
-    const long long idx = (long long)j * G.sj + (long long)iu * G.su + (long long)iv * G.sv;
-    rs[idx] = proj[idx] * ray_sec(__ldg(vr + iv).x, cols[col].invD);
+    const long long base = (long long)j * G.sj + (long long)iu * G.su;
+    const int iva = G.nv - 1 - p;
+    const float sec = ray_sec(__ldg(vr + iva).x, cols[col].invD);  // same for the mirror row
+    const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
+    rs[ia] = proj[ia] * sec;
+    if (p != iva) rs[ib] = proj[ib] * sec;
 }
 
-// Adjoint gather: CTA = one xy voxel column (ix, iy) and up to 256 z layers,
-// thread = kLayersPerThread layers (k, k + 64, ...).  For every crossing
-// (view j, detector column iu, xy interval [sa, sb]) of the voxel column, the
-// rows whose rays pass through layer k inside [sa, sb] form a short interval
-// of heights v (ray z = v * (s0 + s) * rKD, so v in [zl, zh] / ((s0 + s) rKD));
-// each candidate row is checked with the exact piece length, the same
-// expression the forward walk evaluates.
+// Adjoint gather: CTA = one xy voxel column (ix, iy), thread = kLayersPerThread
+// mirror pairs of z layers (upper layer ku = nz-1-p, lower layer p).  For every
+// crossing (view j, detector column iu, xy interval [sa, sb]) of the voxel
+// column, the rows whose rays pass through layer ku inside [sa, sb] form a
+// short interval of heights v (ray z = v * (s0 + s) * rKD, so
+// v in [zl, zh] / ((s0 + s) rKD)); each candidate row r is checked with the
+// exact piece length -- the expression the forward walk evaluates -- which is
+// also the length of row nv-1-r in layer p.
 __global__ void __launch_bounds__(kGatherThreads)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
@@ -180,16 +204,19 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 {
     constexpr int L = kLayersPerThread;
     const int cell = blockIdx.x;
-    const int kb = blockIdx.y * kGatherThreads * L + threadIdx.x;
-    float zlo[L], acc[L];
-    bool kok[L];
+    const int pb = blockIdx.y * kGatherThreads * L + threadIdx.x;
+    const int nlp = (G.nz + 1) >> 1;  // layer pairs (the middle layer of an odd nz pairs with itself)
+    float zlo[L], accu[L], accd[L];
+    bool pok[L];
 #pragma unroll
     for (int q = 0; q < L; ++q) {
-        const int k = kb + q * kGatherThreads;
-        kok[q] = k < G.nz;
-        zlo[q] = (float)k - G.halfnz;  // centred coordinate of the layer's lower plane
-        acc[q] = 0.f;
+        const int p = pb + q * kGatherThreads;
+        pok[q] = p < nlp;
+        zlo[q] = (float)(G.nz - 1 - p) - G.halfnz;  // lower plane of the upper layer (>= -0.5)
+        accu[q] = 0.f;
+        accd[q] = 0.f;
     }
+    const int nvm1 = G.nv - 1;
     const int h0 = __ldg(hit_ptr + cell), h1 = __ldg(hit_ptr + cell + 1);
     for (int h = h0; h < h1; ++h) {
         const CellHit e = __ldg(hits + h);
@@ -207,13 +234,19 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
             int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
             ilo = max(ilo, 0);
-            ihi = kok[q] ? min(ihi, G.nv - 1) : -1;
+            ihi = pok[q] ? min(ihi, nvm1) : -1;
             auto cand = [&](int iv) {
                 const float inv = KD * __ldg(vr + iv).y;
                 const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
                 // the ray is inside the layer between its two plane crossings
                 const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
-                if (len > 0.f) acc[q] = fmaf(len, __ldg(rsc + iv * G.sv32), acc[q]);
+                if (len > 0.f) {
+                    accu[q] = fmaf(len, __ldg(rsc + iv * G.sv32), accu[q]);
+                    // the middle row of an odd nv (v = 0) is its own mirror and
+                    // belongs to the upper layer only
+                    if (2 * iv != nvm1)
+                        accd[q] = fmaf(len, __ldg(rsc + (nvm1 - iv) * G.sv32), accd[q]);
+                }
             };
             if (ilo <= ihi) cand(ilo);
             if (ilo + 1 <= ihi) cand(ilo + 1);
@@ -221,16 +254,22 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
         }
     }
+    float *colv = vol + (long long)cell * G.nz;
 #pragma unroll
-    for (int q = 0; q < L; ++q)
-        if (kok[q]) vol[(long long)cell * G.nz + kb + q * kGatherThreads] += acc[q];
+    for (int q = 0; q < L; ++q) {
+        if (!pok[q]) continue;
+        const int p = pb + q * kGatherThreads, ku = G.nz - 1 - p;
+        colv[ku] += accu[q];
+        if (p != ku) colv[p] += accd[q];
+    }
 }
 
 }  // namespace
 
 int project_blocks(const ProjGeom &g)
 {
-    const int nrgb = (g.nv + 32 * kRowGroups - 1) / (32 * kRowGroups);
+    const int np = (g.nv + 1) >> 1;
+    const int nrgb = (np + 32 * kRowGroups - 1) / (32 * kRowGroups);
     return g.n_views * g.nu * nrgb;
 }
 
@@ -265,8 +304,9 @@ cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float
     const int nb = project_blocks(g);
     if (nb <= 0) return cudaSuccess;
     scale_rays_kernel<<<nb, 256, 0, st>>>(g, cols, vr, proj, rs);
-    const int per_cta = kGatherThreads * kLayersPerThread;
-    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((g.nz + per_cta - 1) / per_cta));
+    const int per_cta = kGatherThreads * kLayersPerThread;  // layer pairs per CTA
+    const int nlp = (g.nz + 1) >> 1;
+    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((nlp + per_cta - 1) / per_cta));
     adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol);
     return cudaGetLastError();
 }
