@@ -227,14 +227,20 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
         // candidate bounds only: the rows are then checked exactly
         const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
         const float *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
+        const float *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
 #pragma unroll
         for (int q = 0; q < L; ++q) {
             const float zl = zlo[q], zh = zl + 1.f;
-            const float vlo = fminf(zl * rGa, zl * rGb), vhi = fmaxf(zh * rGa, zh * rGb);
+            // G grows with s, so 1/G(sa) >= 1/G(sb); upper layers have zl >= 0
+            // except the middle layer of an odd nz (zl = -0.5)
+            const float vlo = zl * (zl >= 0.f ? rGb : rGa), vhi = zh * rGa;
             int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
             int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
             ilo = max(ilo, 0);
             ihi = pok[q] ? min(ihi, nvm1) : -1;
+            // only a layer touching z = 0 can hold the middle row of an odd nv
+            // (v = 0), which is its own mirror and belongs to the upper layer
+            const bool mid = zl < 1.f && (nvm1 & 1) == 0;
             auto cand = [&](int iv) {
                 const float inv = KD * __ldg(vr + iv).y;
                 const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
@@ -242,10 +248,8 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                 const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
                 if (len > 0.f) {
                     accu[q] = fmaf(len, __ldg(rsc + iv * G.sv32), accu[q]);
-                    // the middle row of an odd nv (v = 0) is its own mirror and
-                    // belongs to the upper layer only
-                    if (2 * iv != nvm1)
-                        accd[q] = fmaf(len, __ldg(rsc + (nvm1 - iv) * G.sv32), accd[q]);
+                    if (!mid || 2 * iv != nvm1)
+                        accd[q] = fmaf(len, __ldg(rsm - iv * G.sv32), accd[q]);
                 }
             };
             if (ilo <= ihi) cand(ilo);
