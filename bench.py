@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -80,19 +81,29 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def code_digest(path):
+    """sha256 of a C/CUDA source with its comments and blank lines removed, so
+    that a comment edit does not invalidate counters taken on the same code."""
+    with open(path) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def traffic_record(kernel):
     """Per-launch DRAM traffic from a committed ncu summary, valid only while
-    the projector source is unchanged since the counters were taken."""
+    the projector code is unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "projector_traffic.json")
     src = os.path.join(ROOT, "paper_2509_08574_gb300", "csrc", "kernels_project.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
+        h = code_digest(src)
     except OSError:
         return None
-    if rec.get("source_sha256") != h:
+    if rec.get("code_sha256") != h:
         return None
     total = 0.0
     for name in kernel.split("+"):

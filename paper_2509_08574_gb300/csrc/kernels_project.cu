@@ -6,9 +6,10 @@
 // the text after the augmented system), so these two kernels carry nearly all
 // of the bytes of a reconstruction.
 //
-// Layout of the work: one warp = 32 consecutive detector rows of one detector
-// column of one view; one CTA = 8 such warps of the same column (256 rows),
-// so the column's cell list is fetched from DRAM once per CTA.  Because the detector v
+// Layout of the work: one thread = one pair of mirror rows (below), one warp =
+// 32 consecutive pairs of one detector column of one view, one CTA = 8 such
+// warps of the same column (512 rows), so the column's cell list is fetched
+// from DRAM once per CTA.  Because the detector v
 // axis is parallel to the rotation axis and the source lies in z = 0, every
 // ray of a column has the same xy path.  That path is walked once per
 // geometry on the host (FP64, ray_tables.h) and stored as the column's cell
@@ -19,11 +20,11 @@
 // z voxels of one z-fastest voxel column, so the forward gathers coalesce into
 // one or two 32-byte sectors.
 //
-// The adjoint is a gather over the transpose of the same tables: one thread
-// per voxel (one CTA per xy voxel column) visits every detector column that
-// crosses its voxel column and, for the two or three rows whose rays cross its
-// z layer there, adds piece length x ray value -- no atomics, one store per
-// voxel, deterministic.  Both kernels evaluate the same piece lengths
+// The adjoint is a gather over the transpose of the same tables: one CTA per
+// xy voxel column, one thread per two pairs of mirror layers, visits every
+// detector column that crosses its voxel column and, for the two or three rows
+// whose rays cross each of its z layers there, adds piece length x ray value
+// -- no atomics, one store per voxel, deterministic.  Both kernels evaluate the same piece lengths
 //   len = min(s_exit_xy, s_z(exit plane)) - max(s_enter_xy, s_z(entry plane))
 // from the same FP32 cell boundaries and the same plane-crossing formula
 // fma(kc, KD / v, -s0), with the exact plane coordinate kc (never an
