@@ -23,6 +23,7 @@ _lib = None
 
 PICCS, PIPLE, TV, CGLS = 0, 1, 2, 3
 RULE_R1, RULE_R2 = 0, 1
+SOLVER_CGLS, SOLVER_LSQR, SOLVER_LSQR_REORTH = 0, 1, 2
 
 
 class _Geom(C.Structure):
@@ -68,7 +69,8 @@ def _load():
             lib.og_grad_adj.argtypes = [i, i, i, pd, pd]
             lib.og_weights.argtypes = [ll, pd, d, i, pd]
             lib.og_cgls_fixed.argtypes = [pg, pd, pd, pd, pd, d, d, i, pd, i, pd, i]
-            lib.og_irn.argtypes = [pg, pd, pd, pd, d, d, d, i, i, i, i, pd, pd, i]
+            lib.og_lsqr_fixed.argtypes = [pg, pd, pd, pd, pd, d, d, i, pd, i, i, pd, pd, i]
+            lib.og_irn.argtypes = [pg, pd, pd, pd, d, d, d, i, i, i, i, i, pd, pd, i]
             _lib = lib
     return _lib
 
@@ -188,10 +190,33 @@ def cgls_fixed(g, b, xp, w1, w2, alpha, lam, variant, x0, iters, nthreads: int =
     return x.reshape(g.vol_shape()), res[:n + 1]
 
 
+def lsqr_fixed(g, b, xp, w1, w2, alpha, lam, variant, x0, iters, reorth: bool = False,
+               nthreads: int = 0, return_basis: bool = False):
+    """LSQR on the augmented system with fixed weights; returns (x, residuals)
+    and, with return_basis, the bidiagonalisation's v vectors (rows).
+    reorth: re-orthogonalise every new v against all earlier ones."""
+    lib = _load()
+    x = _f64(x0).reshape(-1).copy()
+    b = _f64(b).reshape(-1)
+    xp = _f64(xp).reshape(-1)
+    w1 = _f64(w1).reshape(-1)
+    w2 = _f64(w2).reshape(-1)
+    res = np.full(iters + 1, np.nan)
+    V = np.zeros((iters + 1, g.M)) if return_basis else None
+    n = lib.og_lsqr_fixed(_GeomHandle(g).ref, _pd(b), _pd(xp), _pd(w1), _pd(w2),
+                          alpha, lam, variant, _pd(x), iters, int(bool(reorth)), _pd(res),
+                          _pd(V) if V is not None else None, nthreads)
+    if n < 0:
+        raise ValueError("invalid geometry")
+    if return_basis:
+        return x.reshape(g.vol_shape()), res[:n + 1], V[:n + 1]
+    return x.reshape(g.vol_shape()), res[:n + 1]
+
+
 def irn(g, b, xp, x0, alpha, lam, tau, n_outer, n_inner, variant=PICCS, rule=RULE_R1,
-        nthreads: int = 0):
-    """IRN outer loop with CGLS inner solves; returns (x, residual history,
-    last weights (w1, w2))."""
+        nthreads: int = 0, solver: int = SOLVER_CGLS):
+    """IRN outer loop with CGLS (or LSQR) inner solves; returns (x, residual
+    history, last weights (w1, w2))."""
     lib = _load()
     x = _f64(x0).reshape(-1).copy()
     b = _f64(b).reshape(-1)
@@ -199,7 +224,7 @@ def irn(g, b, xp, x0, alpha, lam, tau, n_outer, n_inner, variant=PICCS, rule=RUL
     res = np.full(n_outer * (n_inner + 1), np.nan)
     w = np.zeros(2 * g.M)
     rc = lib.og_irn(_GeomHandle(g).ref, _pd(b), _pd(xp), _pd(x), alpha, lam, tau, rule,
-                    variant, n_outer, n_inner, _pd(res), _pd(w), nthreads)
+                    variant, n_outer, n_inner, int(solver), _pd(res), _pd(w), nthreads)
     if rc != 0:
         raise ValueError("invalid geometry")
     return (x.reshape(g.vol_shape()), res.reshape(n_outer, n_inner + 1),

@@ -22,6 +22,9 @@
  *     W2 = W(D x_{k-1} - D x_p), then a few CGLS iterations on the augmented
  *     least-squares problem [A; alpha W1 D; lambda W2 D] x ~ [b; 0; lambda W2 D x_p]
  *     warm-started at x_{k-1}, with the augmented residual kept explicitly;
+ *     LSQR (Golub-Kahan bidiagonalisation, optionally with the new v
+ *     re-orthogonalised against all earlier ones) may replace CGLS, as the
+ *     paper allows (Sec. 2.3);
  *   - variants: IRN-PIPLE (Eq. 8: the prior block becomes lambda I, right-hand
  *     side lambda x_p), IRN-TV (Eq. 6: no prior block) and plain CGLS.
  *
@@ -558,6 +561,130 @@ static int og_cgls_core(og_aug *a, const double *bt, double *x, int iters, doubl
     return done;
 }
 
+/* LSQR (Paige and Saunders' Golub-Kahan form, the Krylov method Sec. 2.3
+ * names as mathematically equivalent to CGLS) on A~ x ~ b~ with FIXED
+ * weights, started at x.  Steps, with u, v, w the bidiagonalisation and
+ * search vectors:
+ *   beta1 u1 = b~ - A~ x0,  alpha1 v1 = A~^T u1,  w1 = v1,
+ *   phibar1 = beta1,  rhobar1 = alpha1;  then for each step i
+ *   beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
+ *   alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i
+ *   rho_i = |(rhobar_i, beta_{i+1})|,  c_i = rhobar_i / rho_i,  s_i = beta_{i+1} / rho_i
+ *   theta_{i+1} = s_i alpha_{i+1},  rhobar_{i+1} = -c_i alpha_{i+1}
+ *   phi_i = c_i phibar_i,  phibar_{i+1} = s_i phibar_i
+ *   x_i = x_{i-1} + (phi_i / rho_i) w_i,  w_{i+1} = v_{i+1} - (theta_{i+1} / rho_i) w_i.
+ * reorth != 0: every new v is re-orthogonalised against all earlier v by
+ * classical Gram-Schmidt applied twice, before its norm is taken.
+ * Stops like og_cgls_core: once ||A~^T r_i|| = phibar_{i+1} alpha_{i+1} |c_i|
+ * falls to 1e-13 of ||A~^T r_0|| = alpha1 beta1, or when a bidiagonal entry
+ * vanishes (the least-squares solution has been reached).
+ * resid[i] (if given) = ||b~ - A~ x_i||^2 computed explicitly.
+ * basis_out (if given, (iters + 1) x M) receives v_1, v_2, ... in order.
+ * Returns the number of steps taken. */
+static int og_lsqr_core(og_aug *a, const double *bt, double *x, int iters, int reorth,
+                        double *resid, double *basis_out)
+{
+    const long long M = a->M, R = a->R;
+    double *u = (double *)malloc((size_t)R * sizeof(double));
+    double *q = (double *)malloc((size_t)R * sizeof(double));
+    double *v = (double *)malloc((size_t)M * sizeof(double));
+    double *t = (double *)malloc((size_t)M * sizeof(double));
+    double *w = (double *)malloc((size_t)M * sizeof(double));
+    double *V = reorth ? (double *)malloc((size_t)(iters + 1) * (size_t)M * sizeof(double)) : 0;
+    double *h = (double *)malloc((size_t)(iters + 1) * sizeof(double));
+    int done = 0;
+    og_aug_apply(a, x, q);
+    for (long long i = 0; i < R; ++i) u[i] = bt[i] - q[i];
+    double beta = sqrt(og_dot(u, u, R));
+    if (resid) resid[0] = beta * beta;
+    double alpha = 0.0;
+    if (beta > 0.0) {
+        for (long long i = 0; i < R; ++i) u[i] /= beta;
+        og_aug_adjoint(a, u, v);
+        alpha = sqrt(og_dot(v, v, M));
+    }
+    if (alpha > 0.0) {
+        for (long long i = 0; i < M; ++i) v[i] /= alpha;
+        if (V) memcpy(V, v, (size_t)M * sizeof(double));
+        if (basis_out) memcpy(basis_out, v, (size_t)M * sizeof(double));
+        memcpy(w, v, (size_t)M * sizeof(double));
+        double phibar = beta, rhobar = alpha, normar = alpha * beta;
+        const double normar0 = normar;
+        for (int k = 0; k < iters; ++k) {
+            if (!(normar > 1e-13 * normar0)) break;
+            /* beta u <- A~ v - alpha u */
+            og_aug_apply(a, v, q);
+            for (long long i = 0; i < R; ++i) u[i] = q[i] - alpha * u[i];
+            beta = sqrt(og_dot(u, u, R));
+            if (beta > 0.0)
+                for (long long i = 0; i < R; ++i) u[i] /= beta;
+            /* alpha v <- A~^T u - beta v */
+            og_aug_adjoint(a, u, t);
+            for (long long i = 0; i < M; ++i) t[i] -= beta * v[i];
+            if (V) {
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int j = 0; j <= k; ++j) h[j] = og_dot(V + (size_t)j * M, t, M);
+                    for (int j = 0; j <= k; ++j)
+                        for (long long i = 0; i < M; ++i) t[i] -= h[j] * V[(size_t)j * M + i];
+                }
+            }
+            const double alpha_new = sqrt(og_dot(t, t, M));
+            /* one Givens rotation of the lower bidiagonal */
+            const double rho = hypot(rhobar, beta);
+            const double c = rhobar / rho, s = beta / rho;
+            const double theta = s * alpha_new;
+            rhobar = -c * alpha_new;
+            const double phi = c * phibar;
+            phibar = s * phibar;
+            for (long long i = 0; i < M; ++i) x[i] += (phi / rho) * w[i];
+            if (alpha_new > 0.0)
+                for (long long i = 0; i < M; ++i) v[i] = t[i] / alpha_new;
+            for (long long i = 0; i < M; ++i) w[i] = v[i] - (theta / rho) * w[i];
+            if (V && alpha_new > 0.0) memcpy(V + (size_t)(k + 1) * M, v, (size_t)M * sizeof(double));
+            if (basis_out && alpha_new > 0.0)
+                memcpy(basis_out + (size_t)(k + 1) * M, v, (size_t)M * sizeof(double));
+            alpha = alpha_new;
+            normar = phibar * alpha_new * fabs(c);
+            ++done;
+            if (resid) {
+                og_aug_apply(a, x, q);
+                double r2 = 0.0;
+                for (long long i = 0; i < R; ++i) r2 += (bt[i] - q[i]) * (bt[i] - q[i]);
+                resid[done] = r2;
+            }
+            if (!(beta > 0.0) || !(alpha_new > 0.0)) break;
+        }
+    }
+    free(u); free(q); free(v); free(t); free(w); free(h);
+    if (V) free(V);
+    return done;
+}
+
+static void og_aug_init(og_aug *a, const og_geom *g, const double *w1, const double *w2,
+                        double alpha, double lambda, int variant, int nthreads)
+{
+    a->g = g; a->variant = variant; a->alpha = alpha; a->lambda = lambda;
+    a->w1 = w1; a->w2 = w2; a->M = og_M(g); a->N = og_N(g);
+    a->R = og_aug_rows(variant, a->N, a->M); a->nthreads = nthreads;
+    a->tmp3 = (double *)malloc((size_t)(3 * a->M) * sizeof(double));
+    a->tmpM = (double *)malloc((size_t)a->M * sizeof(double));
+}
+
+/* LSQR with given weights (solver 1: plain, 2: with re-orthogonalisation). */
+int og_lsqr_fixed(const og_geom *g, const double *b, const double *xp, const double *w1,
+                  const double *w2, double alpha, double lambda, int variant, double *x,
+                  int iters, int reorth, double *resid, double *basis_out, int nthreads)
+{
+    if (og_check(g) != 0) return -1;
+    og_aug a;
+    og_aug_init(&a, g, w1, w2, alpha, lambda, variant, nthreads);
+    double *bt = (double *)malloc((size_t)a.R * sizeof(double));
+    og_aug_rhs(&a, b, xp, bt);
+    int n = og_lsqr_core(&a, bt, x, iters, reorth, resid, basis_out);
+    free(bt); free(a.tmp3); free(a.tmpM);
+    return n;
+}
+
 /* CGLS with given weights w1, w2 (M each; w2 only used by PICCS). */
 int og_cgls_fixed(const og_geom *g, const double *b, const double *xp, const double *w1,
                   const double *w2, double alpha, double lambda, int variant, double *x,
@@ -579,13 +706,14 @@ int og_cgls_fixed(const og_geom *g, const double *b, const double *xp, const dou
 
 /* IRN outer loop (Sec. 2.3, Eqs. 10-11).  x holds x_0 on entry and the final
  * iterate on exit.  For each outer k the weights are frozen at the previous
- * iterate, then n_inner CGLS steps are taken on the augmented problem,
+ * iterate, then n_inner steps of the inner solver (solver 0: CGLS, 1: LSQR,
+ * 2: LSQR with re-orthogonalisation) are taken on the augmented problem,
  * warm-started at x_{k-1}.  resid (if given) gets n_outer*(n_inner+1) values:
  * the augmented residual before and after every inner step of every cycle.
  * w_out (if given) gets the last cycle's w1 and w2 (2M values). */
 int og_irn(const og_geom *g, const double *b, const double *xp, double *x, double alpha,
            double lambda, double tau, int rule, int variant, int n_outer, int n_inner,
-           double *resid, double *w_out, int nthreads)
+           int solver, double *resid, double *w_out, int nthreads)
 {
     if (og_check(g) != 0) return -1;
     const long long M = og_M(g);
@@ -604,8 +732,12 @@ int og_irn(const og_geom *g, const double *b, const double *xp, double *x, doubl
             og_grad(g->nx, g->ny, g->nz, dif, g3);
             og_weights(M, g3, tau, rule, w2);
         }
-        og_cgls_fixed(g, b, xp, w1, w2, alpha, lambda, variant, x, n_inner,
-                      resid ? resid + (size_t)k * (n_inner + 1) : 0, nthreads);
+        double *rk = resid ? resid + (size_t)k * (n_inner + 1) : 0;
+        if (solver == 0)
+            og_cgls_fixed(g, b, xp, w1, w2, alpha, lambda, variant, x, n_inner, rk, nthreads);
+        else
+            og_lsqr_fixed(g, b, xp, w1, w2, alpha, lambda, variant, x, n_inner, solver == 2, rk,
+                          0, nthreads);
     }
     if (w_out) {
         memcpy(w_out, w1, (size_t)M * sizeof(double));

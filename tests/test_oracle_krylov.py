@@ -1,8 +1,8 @@
-"""Pins for the oracle's CGLS inner solver and IRN outer loop (CPU only).
+"""Pins for the oracle's CGLS and LSQR inner solvers and IRN outer loop (CPU only).
 
 The inner problem is the augmented least-squares system of Sec. 2.3
-[A; alpha W1 D; lambda W2 D] x ~ [b; 0; lambda W2 D x_p], solved by CGLS (the
-paper's choice; LSQR is mathematically equivalent).  These tests build the
+[A; alpha W1 D; lambda W2 D] x ~ [b; 0; lambda W2 D x_p], solved by CGLS or
+by LSQR (mathematically equivalent, Sec. 2.3).  These tests build the
 same system densely from independently pinned pieces (A column by column, D
 from Kronecker products) and compare with numpy/scipy solvers; the IRN loop is
 pinned by the majorisation-minimisation decrease of the smoothed objective.
@@ -92,13 +92,9 @@ def test_unregularised_cgls_is_least_squares(small):
     np.testing.assert_allclose(x.reshape(-1), x_ref, rtol=0, atol=1e-6 * np.abs(x_ref).max())
 
 
-@pytest.mark.parametrize("variant", [O.PICCS, O.PIPLE])
-@pytest.mark.parametrize("k", [1, 2, 5, 8])
-def test_iterate_k_is_krylov_subspace_minimiser(small, variant, k):
-    """x_k = x_0 + argmin over K_k(At^T At, At^T r_0) of ||At x - bt||."""
-    g = small["g"]
-    At, bt = _dense_aug(small, variant, 0.5, 0.6)
-    x0 = small["xp"].copy()
+def _krylov_minimiser(At, bt, x0, k):
+    """x_0 + argmin over K_k(At^T At, At^T r_0) of ||At x - bt||, from an
+    orthonormal basis of the Krylov space and a dense least-squares solve."""
     r0 = bt - At @ x0
     AtA = At.T @ At
     v = At.T @ r0
@@ -113,10 +109,75 @@ def test_iterate_k_is_krylov_subspace_minimiser(small, variant, k):
         v = AtA @ v
     K = np.stack(basis, 1)
     z = np.linalg.lstsq(At @ K, r0, rcond=None)[0]
-    x_ref = x0 + K @ z
+    return x0 + K @ z
+
+
+@pytest.mark.parametrize("variant", [O.PICCS, O.PIPLE])
+@pytest.mark.parametrize("k", [1, 2, 5, 8])
+def test_iterate_k_is_krylov_subspace_minimiser(small, variant, k):
+    """x_k = x_0 + argmin over K_k(At^T At, At^T r_0) of ||At x - bt||."""
+    g = small["g"]
+    At, bt = _dense_aug(small, variant, 0.5, 0.6)
+    x0 = small["xp"].copy()
+    x_ref = _krylov_minimiser(At, bt, x0, k)
     x, _ = O.cgls_fixed(g, small["b"], small["xp"], small["w1"], small["w2"], 0.5, 0.6,
                         variant, x0, k)
     np.testing.assert_allclose(x.reshape(-1), x_ref, rtol=0, atol=1e-9 * np.abs(x_ref).max())
+
+
+@pytest.mark.parametrize("reorth", [False, True])
+@pytest.mark.parametrize("variant", [O.PICCS, O.PIPLE, O.TV, O.CGLS])
+@pytest.mark.parametrize("k", [1, 3, 10])
+def test_oracle_lsqr_matches_scipy_lsqr(small, variant, k, reorth):
+    """The oracle's LSQR against scipy's (Paige-Saunders) on the dense system."""
+    g = small["g"]
+    At, bt = _dense_aug(small, variant, 0.6, 0.45)
+    x0 = small["xp"].copy()
+    x_ref = lsqr(At, bt, x0=x0, iter_lim=k, atol=0, btol=0, conlim=0)[0]
+    x, res = O.lsqr_fixed(g, small["b"], small["xp"], small["w1"], small["w2"], 0.6, 0.45,
+                          variant, x0, k, reorth=reorth)
+    assert len(res) == k + 1
+    np.testing.assert_allclose(x.reshape(-1), x_ref, rtol=0, atol=1e-9 * np.abs(x_ref).max())
+    np.testing.assert_allclose(res, [np.sum((bt - At @ x0) ** 2)] + list(res[1:]))
+    assert abs(res[-1] - np.sum((bt - At @ x_ref) ** 2)) <= 1e-9 * res[0]
+
+
+@pytest.mark.parametrize("variant", [O.PICCS, O.PIPLE])
+@pytest.mark.parametrize("k", [2, 5, 8])
+def test_lsqr_iterate_is_krylov_subspace_minimiser(small, variant, k):
+    g = small["g"]
+    At, bt = _dense_aug(small, variant, 0.5, 0.6)
+    x0 = np.zeros(g.M)
+    x_ref = _krylov_minimiser(At, bt, x0, k)
+    for reorth in (False, True):
+        x, _ = O.lsqr_fixed(g, small["b"], small["xp"], small["w1"], small["w2"], 0.5, 0.6,
+                            variant, x0, k, reorth=reorth)
+        np.testing.assert_allclose(x.reshape(-1), x_ref, rtol=0,
+                                   atol=1e-9 * np.abs(x_ref).max())
+
+
+def test_converged_lsqr_with_reorthogonalisation_solves_normal_equations(small):
+    """With full re-orthogonalisation the bidiagonalisation terminates in at
+    most M steps in exact arithmetic; the stop rule must then end the loop
+    early, at the least-squares solution."""
+    g = small["g"]
+    At, bt = _dense_aug(small, O.PICCS, 0.7, 0.4)
+    x_ref = np.linalg.solve(At.T @ At, At.T @ bt)
+    x, res = O.lsqr_fixed(g, small["b"], small["xp"], small["w1"], small["w2"], 0.7, 0.4,
+                          O.PICCS, np.zeros(g.M), 4 * g.M, reorth=True)
+    assert len(res) - 1 < 4 * g.M
+    np.testing.assert_allclose(x.reshape(-1), x_ref, rtol=0, atol=1e-8 * np.abs(x_ref).max())
+    assert np.all(np.diff(res) <= 1e-12 * res[0])
+
+
+@pytest.mark.parametrize("solver", [O.SOLVER_LSQR, O.SOLVER_LSQR_REORTH])
+def test_irn_with_lsqr_equals_irn_with_cgls(small, solver):
+    g = small["g"]
+    a, ra, _ = O.irn(g, small["b"], small["xp"], small["xp"], 0.5, 0.5, 0.05, 3, 5)
+    b, rb, _ = O.irn(g, small["b"], small["xp"], small["xp"], 0.5, 0.5, 0.05, 3, 5,
+                     solver=solver)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-9 * np.abs(a).max())
+    np.testing.assert_allclose(rb, ra, rtol=1e-8)
 
 
 @pytest.mark.parametrize("k", [3, 10])
@@ -206,3 +267,26 @@ def test_cgls_variant_ignores_regularisation(small):
     b, _ = O.cgls_fixed(g, small["b"], small["xp"], small["w1"], small["w2"], 0.0, 0.0,
                         O.CGLS, np.zeros(g.M), 6)
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_lsqr_reorthogonalisation_keeps_the_basis_orthonormal():
+    """Golub-Kahan in floating point loses the orthogonality of V within a few
+    tens of steps on this system; re-orthogonalised, V stays orthonormal to
+    rounding, and the bidiagonal relation A~^T u_{k+1} = alpha_{k+1} v_{k+1}
+    + beta_{k+1} v_k keeps consecutive v's tied to the operator."""
+    g = P.tiny_geometry(n=(6, 6, 5), det=(10, 8), n_views=12, dso=40.0, dsd=60.0)
+    rng = np.random.default_rng(7)
+    b = rng.normal(size=g.N)
+    xp = rng.normal(size=g.M)
+    w1 = rng.uniform(0.5, 2.0, g.M)
+    w2 = rng.uniform(0.5, 2.0, g.M)
+    k = 30
+    _, _, V = O.lsqr_fixed(g, b, xp, w1, w2, 0.3, 0.2, O.PICCS, np.zeros(g.M), k,
+                           reorth=True, return_basis=True)
+    assert V.shape == (k + 1, g.M)
+    assert np.abs(V @ V.T - np.eye(k + 1)).max() < 1e-12
+    _, _, V0 = O.lsqr_fixed(g, b, xp, w1, w2, 0.3, 0.2, O.PICCS, np.zeros(g.M), k,
+                            reorth=False, return_basis=True)
+    assert np.abs(V0 @ V0.T - np.eye(k + 1)).max() > 1e-3
+    # the first vectors agree while the plain recurrence is still orthogonal
+    np.testing.assert_allclose(V0[:6], V[:6], rtol=0, atol=1e-9)
