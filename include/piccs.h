@@ -72,6 +72,16 @@ enum { PICCS_WEIGHT_R1 = 0, PICCS_WEIGHT_R2 = 1 };
 /* Initial guess: the prior x_p (default), zero, or a caller volume. */
 enum { PICCS_X0_PRIOR = 0, PICCS_X0_ZERO = 1, PICCS_X0_USER = 2 };
 
+/* Inner Krylov solver (Sec. 2.3: LSQR, or the mathematically equivalent
+ * CGLS).  CGLS: Hestenes-Stiefel recurrences.  LSQR: Golub-Kahan
+ * bidiagonalisation of the augmented operator with a Givens QR update (one
+ * more forward projection per cycle than CGLS).  LSQR_REORTH: LSQR with each
+ * new v re-orthogonalised against the cycle's earlier ones (classical
+ * Gram-Schmidt, twice); the first such reconstruction on a context allocates
+ * (n_inner - 1) * M floats for the basis (PICCS_ENOMEM if the device lacks
+ * them) and keeps them; n_inner - 1 must not exceed 256. */
+enum { PICCS_SOLVER_CGLS = 0, PICCS_SOLVER_LSQR = 1, PICCS_SOLVER_LSQR_REORTH = 2 };
+
 typedef struct {
     int nx, ny, nz;            /* voxels */
     double vx, vy, vz;         /* voxel size, mm (> 0) */
@@ -94,6 +104,7 @@ typedef struct {
     int x0_mode;               /* PICCS_X0_* */
     int variant;               /* PICCS_VARIANT_* */
     int weight_rule;           /* PICCS_WEIGHT_* */
+    int solver;                /* PICCS_SOLVER_* */
 } piccs_params;
 
 /* What the last reconstruction did (filled by piccs_report, which waits). */
@@ -102,7 +113,9 @@ typedef struct {
     int iterations_run;        /* inner iterations that changed x */
     int n_history;             /* entries written to gamma_history */
     double gamma_history[512]; /* ||A~^T r~||^2 at the start of each cycle and
-                                  after every inner iteration, in order */
+                                  after every inner iteration, in order (LSQR:
+                                  not after the last iteration of a cycle, whose
+                                  value would cost one more backprojection) */
 } piccs_stats;
 
 /* Kernel accounting of a context (see piccs_profile_enable). */
@@ -136,8 +149,9 @@ const char *piccs_last_error(const piccs_ctx *ctx);
 /* Change the stream later calls enqueue on. */
 int piccs_set_stream(piccs_ctx *ctx, void *cuda_stream);
 
-/* Device bytes piccs_create allocates for this geometry (params may be NULL).
- * Pure host computation; needs no GPU. */
+/* Device bytes piccs_create allocates for this geometry (params may be NULL),
+ * plus, when params->solver is PICCS_SOLVER_LSQR_REORTH, the basis the first
+ * such reconstruction allocates.  Pure host computation; needs no GPU. */
 int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
                           size_t *bytes);
 

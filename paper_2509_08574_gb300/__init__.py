@@ -30,6 +30,7 @@ LAYOUT_UV, LAYOUT_VU = 0, 1
 VARIANT_PICCS, VARIANT_PIPLE, VARIANT_TV, VARIANT_CGLS = 0, 1, 2, 3
 WEIGHT_R1, WEIGHT_R2 = 0, 1
 X0_PRIOR, X0_ZERO, X0_USER = 0, 1, 2
+SOLVER_CGLS, SOLVER_LSQR, SOLVER_LSQR_REORTH = 0, 1, 2
 
 _NAMES = {0: "PICCS_OK", -1: "PICCS_EINVAL", -2: "PICCS_ENOMEM", -3: "PICCS_ENONFINITE",
           -4: "PICCS_EBREAKDOWN", -5: "PICCS_ETIMEOUT", -6: "PICCS_ECUDA", -7: "PICCS_ENOTIMPL"}
@@ -54,7 +55,7 @@ class piccs_geometry(C.Structure):
 class piccs_params(C.Structure):
     _fields_ = [("alpha", C.c_float), ("lambda_", C.c_float), ("tau", C.c_float),
                 ("n_outer", C.c_int), ("n_inner", C.c_int), ("x0_mode", C.c_int),
-                ("variant", C.c_int), ("weight_rule", C.c_int)]
+                ("variant", C.c_int), ("weight_rule", C.c_int), ("solver", C.c_int)]
 
 
 class piccs_stats(C.Structure):
@@ -162,8 +163,8 @@ def make_geometry(g):
 
 
 def make_params(alpha=0.5, lam=0.5, tau=1e-2, n_outer=1, n_inner=10, x0_mode=X0_PRIOR,
-                variant=VARIANT_PICCS, weight_rule=WEIGHT_R1):
-    return piccs_params(alpha, lam, tau, n_outer, n_inner, x0_mode, variant, weight_rule)
+                variant=VARIANT_PICCS, weight_rule=WEIGHT_R1, solver=SOLVER_CGLS):
+    return piccs_params(alpha, lam, tau, n_outer, n_inner, x0_mode, variant, weight_rule, solver)
 
 
 def _stream_handle(stream):

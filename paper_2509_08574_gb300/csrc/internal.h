@@ -61,14 +61,45 @@ struct KrylovScalars {
     double hist[512];
 };
 
-enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1 };
+constexpr int kMaxBasis = 256;  // LSQR re-orthogonalisation: basis vectors per cycle
+
+// Device-side state of LSQR (Golub-Kahan bidiagonalisation of the augmented
+// operator with the Givens QR update).  The augmented vector u is held as
+// beta * u = [uA; R z + sigma b_R] (R the regularisation rows, b_R their
+// right-hand side), so its 3M or 6M regularisation rows are never stored:
+// R^T (R z + sigma b_R) = K z + sigma c with K = D^T Omega D (+ lambda^2 I for
+// PIPLE), c = R^T b_R, and |R z + sigma b_R|^2 = z.K z + 2 sigma <z, c> +
+// sigma^2 |b_R|^2, |b_R|^2 = <x_p, c>.  v is stored unnormalised (vhat =
+// alpha v).  The float blocks are the coefficients the vector and projector
+// kernels read; the finalize kernels write them.
+struct LsqrScalars {
+    double alpha, beta;   // alpha_i (= |vhat|) and beta_i (uA and z are beta_i u_i)
+    double rhobar, phibar, c, s, rho;
+    double sigma;         // coefficient of b_R in beta_i u_i
+    double sigma_next;    // coefficient of b_R after the next z-step
+    double bR2;           // |b_R|^2 = <x_p, c>
+    double normar0;       // |A~^T r~| at the start of the cycle
+    int stopped;          // the cycle has converged or a bidiagonal entry vanished
+    int nbasis;           // vectors held in the re-orthogonalisation basis
+    float fwd[4];         // forward u-step: {1/alpha_i, alpha_i/beta_i, stopped, 0}
+    float ureg[4];        // z-step: {1/alpha_i, alpha_i/beta_i, new sigma, stopped}
+    float vx[8];          // {1/alpha_i, theta_i/rho_{i-1}, phi_i/rho_i, 1/beta_{i+1},
+                          //  beta_{i+1}, stopped, first step of the cycle, 0}
+    double h[kMaxBasis];  // Gram-Schmidt coefficients
+};
+
+enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_LSQR = 2 };
 
 // ---- projector (kernels_project.cu) ----
 int project_blocks(const ProjGeom &g);
 // vr[iv] = {v, 1/v} per detector row (1e30 for v = 0)
+// mode FWD_PLAIN: out = A vol; FWD_RESID: out = aux - A vol (aux = the data b,
+// NaN/Inf in it set *nonfinite); FWD_LSQR: out = aux[0] A vol - aux[1] out, and
+// nothing when aux[2] != 0 (aux = LsqrScalars::fwd).  partials (may be null)
+// get |out|^2 per block.
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
-                           const float *b, double *partials, int *nonfinite, cudaStream_t st);
+                           const float *aux, double *partials, int *nonfinite, cudaStream_t st);
 // vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
 // N-float scratch that receives proj scaled by each ray's sec.
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
@@ -93,6 +124,16 @@ cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, fl
                                const float *c, float *g, float *s, int first, double *partials,
                                cudaStream_t st);
 
+// LSQR z-step and the regularisation part of A~^T u (see LsqrScalars):
+// init: z' = -src, sigma' = 1; else z' = co[0] src - co[1] z (co = LsqrScalars::ureg,
+// sigma' = co[2]); then s = K z' + sigma' c.  partials: 2 (init: 3) arrays of
+// stencil_blocks(M) doubles, [z'.K z' | <z', c> | <x_p, c>].  Skipped when
+// co[3] != 0 (not in init).
+cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
+                             float *znew, const float *omega, float lam2_piple, const float *c,
+                             const float *xp, float *s, const float *co, double *partials,
+                             cudaStream_t st);
+
 // ---- Krylov vector work (kernels_krylov.cu) ----
 int vector_blocks();
 cudaError_t launch_p_update(long long M, const float *s, float *p, const KrylovScalars *k,
@@ -108,6 +149,35 @@ cudaError_t launch_finalize_gamma(KrylovScalars *k, const double *p, int n, int 
 cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st);
 cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st);
 cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st);
+// LSQR
+cudaError_t launch_lsqr_reset(KrylovScalars *k, LsqrScalars *l, cudaStream_t st);
+// first: vhat = s / beta_1; else v = vhat / alpha_i, w = v - tw w, x += tx w and,
+// unless last, vhat = s / beta_{i+1} - beta_{i+1} v; basis (may be null) gets v.
+// partials get |vhat|^2 (unless last).
+cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
+                           const float *s, float *basis, const LsqrScalars *l, double *partials,
+                           cudaStream_t st);
+// beta = sqrt(|uA|^2 + z.Kz + 2 sigma <z,c> + sigma^2 |b_R|^2) and the Givens step
+cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
+                                      const double *pu, int nu, const double *pr, int nr,
+                                      cudaStream_t st);
+// alpha = |vhat|, the rest of the Givens step, the stop test
+cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int init,
+                                       const double *p, int n, cudaStream_t st);
+// Basis vector j starts at basis + j * ldb, ldb = lsqr_basis_stride(M) (a
+// multiple of 64 floats, so every vector is 256-byte aligned for float4 access).
+inline long long lsqr_basis_stride(long long M) { return (M + 63) / 64 * 64; }
+// one Gram-Schmidt pass of vhat against basis[0..nb) (nb <= kMaxBasis):
+// dots: partials[j * lsqr_dot_blocks() + block] = <basis_j, vhat>;
+// fin_dots: l->h[j] = their fixed-order sums; sub: vhat -= sum_j h_j basis_j,
+// norm_partials (may be null) get |vhat|^2.  All skip once l->stopped.
+cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
+                             const float *vhat, const LsqrScalars *l, double *partials,
+                             cudaStream_t st);
+cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st);
+cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
+                            const LsqrScalars *l, double *norm_partials, cudaStream_t st);
+int lsqr_dot_blocks();
 
 // ---- host helpers (piccs_api.cpp) ----
 // Sets the per-thread message that piccs_last_error(NULL) returns.

@@ -213,6 +213,276 @@ sum_partials_kernel(const double *p, int n, double *out)
     if (threadIdx.x == 0) *out = t;
 }
 
+// ---------------------------------------------------------------------------
+// LSQR (Golub-Kahan bidiagonalisation with the Givens QR update, the Krylov
+// method Sec. 2.3 names as equivalent to CGLS).  State and notation:
+// LsqrScalars in internal.h.  Per step i the host enqueues: the forward in
+// FWD_LSQR mode (uA <- A vhat / alpha_i - (alpha_i / beta_i) uA), the z-step
+// stencil (kernels_reg.cu), finalize_beta (beta_{i+1}, rho_i, c_i, s_i, phi_i,
+// phibar_{i+1}), the adjoint (s += A^T uA), lsqr_vx (w, x and the next vhat),
+// optionally the re-orthogonalisation, and finalize_alpha (alpha_{i+1},
+// theta_{i+1}, rhobar_{i+1}, the stop test).
+
+__global__ void lsqr_reset_kernel(LsqrScalars *l)
+{
+    l->alpha = l->beta = l->rhobar = l->phibar = l->c = l->s = l->rho = 0.0;
+    l->sigma = l->sigma_next = l->bR2 = l->normar0 = 0.0;
+    l->stopped = 0;
+    l->nbasis = 0;
+    for (int i = 0; i < 4; ++i) l->fwd[i] = l->ureg[i] = 0.f;
+    for (int i = 0; i < 8; ++i) l->vx[i] = 0.f;
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kThreads)
+lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
+               float *__restrict__ vhat, const float *__restrict__ s, float *__restrict__ basis,
+               const LsqrScalars *__restrict__ l, double *__restrict__ partials)
+{
+    const float ia = l->vx[0], tw = l->vx[1], tx = l->vx[2], ib = l->vx[3], bb = l->vx[4];
+    if (!FIRST && l->vx[5] != 0.f) return;
+    const bool wrestart = l->vx[6] != 0.f;  // first step of a cycle: w = v
+    const long long n4 = M >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    auto one = [&](float vh, float si, float &xo, float &wo, float &vo, float &bo) -> float {
+        if (FIRST) {
+            vo = ib * si;
+            return vo * vo;
+        }
+        const float v = ia * vh;
+        const float wn = wrestart ? v : fmaf(-tw, wo, v);
+        xo = fmaf(tx, wn, xo);
+        wo = wn;
+        bo = v;
+        if (LAST) return 0.f;
+        vo = fmaf(ib, si, -bb * v);
+        return vo * vo;
+    };
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    float4 *w4 = reinterpret_cast<float4 *>(w);
+    float4 *v4 = reinterpret_cast<float4 *>(vhat);
+    float4 *b4 = reinterpret_cast<float4 *>(basis);
+    for (long long i = t0; i < n4; i += stride) {
+        const float4 si = LAST ? make_float4(0.f, 0.f, 0.f, 0.f) : s4[i];
+        float4 vh = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : v4[i];
+        float4 xo = make_float4(0.f, 0.f, 0.f, 0.f), wo = xo, bo = xo, vo = vh;
+        if (!FIRST) {
+            xo = x4[i];
+            if (!wrestart) wo = w4[i];
+        }
+        float q = one(vh.x, si.x, xo.x, wo.x, vo.x, bo.x);
+        q += one(vh.y, si.y, xo.y, wo.y, vo.y, bo.y);
+        q += one(vh.z, si.z, xo.z, wo.z, vo.z, bo.z);
+        q += one(vh.w, si.w, xo.w, wo.w, vo.w, bo.w);
+        acc += (double)q;
+        if (!FIRST) {
+            x4[i] = xo;
+            w4[i] = wo;
+            if (basis) b4[i] = bo;
+        }
+        if (!LAST) v4[i] = vo;
+    }
+    for (long long i = (n4 << 2) + t0; i < M; i += stride) {
+        float xo = FIRST ? 0.f : x[i], wo = (FIRST || wrestart) ? 0.f : w[i];
+        float vo = 0.f, bo = 0.f;
+        acc += (double)one(FIRST ? 0.f : vhat[i], LAST ? 0.f : s[i], xo, wo, vo, bo);
+        if (!FIRST) {
+            x[i] = xo;
+            w[i] = wo;
+            if (basis) basis[i] = bo;
+        }
+        if (!LAST) vhat[i] = vo;
+    }
+    if (!LAST) block_sum_store(acc, partials);
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const double *pu, int nu,
+                          const double *pr, int nr)
+{
+    const double u2 = cta_sum(pu, nu);
+    const double zkz = cta_sum(pr, nr);
+    const double zc = cta_sum(pr + nr, nr);
+    const double bR2 = init ? cta_sum(pr + 2 * (long long)nr, nr) : l->bR2;
+    if (threadIdx.x != 0) return;
+    if (!init && l->stopped) return;
+    const double sigma = init ? 1.0 : l->sigma_next;
+    double beta2 = u2 + zkz + 2.0 * sigma * zc + sigma * sigma * bR2;
+    if (!isfinite(beta2)) {
+        if (k->status == 0) k->status = -4;  // PICCS_EBREAKDOWN
+        l->stopped = 1;
+        l->vx[2] = 0.f;
+        l->vx[5] = 1.f;
+        return;
+    }
+    const double beta = sqrt(fmax(beta2, 0.0));
+    l->sigma = sigma;
+    l->beta = beta;
+    l->vx[3] = beta > 0.0 ? (float)(1.0 / beta) : 0.f;
+    l->vx[4] = (float)beta;
+    if (init) {
+        l->bR2 = bR2;
+        l->phibar = beta;
+        l->vx[2] = 0.f;
+        return;
+    }
+    // one Givens rotation eliminates beta_{i+1} below rhobar_i
+    const double rho = hypot(l->rhobar, beta);
+    const double c = l->rhobar / rho, s = beta / rho;
+    const double phi = c * l->phibar;
+    l->phibar = s * l->phibar;
+    l->rho = rho;
+    l->c = c;
+    l->s = s;
+    const double tx = phi / rho;
+    l->vx[2] = isfinite(tx) ? (float)tx : 0.f;
+    if (!isfinite(tx) && k->status == 0) k->status = -4;
+    if (l->vx[2] != 0.f) k->iters_run += 1;
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+lsqr_finalize_alpha_kernel(KrylovScalars *k, LsqrScalars *l, int init, const double *p, int n)
+{
+    const double a2 = cta_sum(p, n);
+    if (threadIdx.x != 0) return;
+    if (l->stopped) return;
+    int stop = 0;
+    double alpha = sqrt(fmax(a2, 0.0));
+    if (!isfinite(alpha)) {
+        if (k->status == 0) k->status = -4;
+        alpha = 0.0;
+        stop = 1;
+    }
+    double normar, tw = 0.0;
+    if (init) {
+        l->rhobar = alpha;
+        normar = alpha * l->beta;
+        l->normar0 = normar;
+        stop |= !(normar > 0.0);
+    } else {
+        const double theta = l->s * alpha;
+        l->rhobar = -l->c * alpha;
+        tw = theta / l->rho;
+        normar = l->phibar * alpha * fabs(l->c);
+        // same rule as CGLS: |A~^T r~| down to 1e-13 of its start, or a
+        // vanishing bidiagonal entry (the least-squares solution is reached)
+        stop |= !(normar > 1e-13 * l->normar0) || !(alpha > 0.0) || !(l->beta > 0.0);
+    }
+    l->alpha = alpha;
+    if (k->n_hist < 512) k->hist[k->n_hist++] = normar * normar;
+    const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    const double kb = l->beta > 0.0 ? alpha / l->beta : 0.0;
+    l->sigma_next = -kb * l->sigma;
+    l->stopped = stop;
+    const float fs = stop ? 1.f : 0.f;
+    l->fwd[0] = (float)ia;
+    l->fwd[1] = (float)kb;
+    l->fwd[2] = fs;
+    l->ureg[0] = (float)ia;
+    l->ureg[1] = (float)kb;
+    l->ureg[2] = (float)l->sigma_next;
+    l->ureg[3] = fs;
+    l->vx[0] = (float)ia;
+    l->vx[1] = (float)tw;
+    l->vx[5] = fs;
+    l->vx[6] = init ? 1.f : 0.f;
+}
+
+// Gram-Schmidt coefficients h_j = <basis_j, vhat>, eight basis vectors per
+// blockIdx.y; one FP64 partial per (j, block) at partials[j * gridDim.x + block]
+constexpr int kDotVecs = 8;
+
+__global__ void __launch_bounds__(kThreads)
+lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
+                 const float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
+                 double *__restrict__ partials)
+{
+    if (l->stopped) return;
+    const int j0 = blockIdx.y * kDotVecs;
+    const int nj = min(kDotVecs, nb - j0);
+    double acc[kDotVecs];
+#pragma unroll
+    for (int q = 0; q < kDotVecs; ++q) acc[q] = 0.0;
+    const long long n4 = M >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const float4 *v4 = reinterpret_cast<const float4 *>(vhat);
+    for (long long i = t0; i < n4; i += stride) {
+        const float4 a = v4[i];
+#pragma unroll
+        for (int q = 0; q < kDotVecs; ++q) {
+            if (q < nj) {
+                const float4 b = reinterpret_cast<const float4 *>(basis + (long long)(j0 + q) * ldb)[i];
+                acc[q] += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+            }
+        }
+    }
+    for (long long i = (n4 << 2) + t0; i < M; i += stride) {
+#pragma unroll
+        for (int q = 0; q < kDotVecs; ++q)
+            if (q < nj) acc[q] += (double)vhat[i] * (double)basis[(long long)(j0 + q) * ldb + i];
+    }
+    __shared__ double red[kDotVecs][kThreads / 32];
+#pragma unroll
+    for (int q = 0; q < kDotVecs; ++q) {
+        double t = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < nj) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += red[threadIdx.x][w];
+        partials[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+lsqr_fin_dots_kernel(LsqrScalars *l, const double *partials, int nblk)
+{
+    const double h = cta_sum(partials + (long long)blockIdx.x * nblk, nblk);
+    if (threadIdx.x == 0) l->h[blockIdx.x] = l->stopped ? 0.0 : h;
+}
+
+// vhat -= sum_j h_j basis_j; partials (may be null) get |vhat|^2
+__global__ void __launch_bounds__(kThreads)
+lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
+                float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
+                double *__restrict__ partials)
+{
+    if (l->stopped) return;
+    const long long n4 = M >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float4 *v4 = reinterpret_cast<float4 *>(vhat);
+    double acc = 0.0;
+    for (long long i = t0; i < n4; i += stride) {
+        float4 a = v4[i];
+        for (int j = 0; j < nb; ++j) {
+            const float h = (float)l->h[j];
+            const float4 b = reinterpret_cast<const float4 *>(basis + (long long)j * ldb)[i];
+            a.x = fmaf(-h, b.x, a.x);
+            a.y = fmaf(-h, b.y, a.y);
+            a.z = fmaf(-h, b.z, a.z);
+            a.w = fmaf(-h, b.w, a.w);
+        }
+        v4[i] = a;
+        acc += (double)fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w)));
+    }
+    for (long long i = (n4 << 2) + t0; i < M; i += stride) {
+        float a = vhat[i];
+        for (int j = 0; j < nb; ++j) a = fmaf(-(float)l->h[j], basis[(long long)j * ldb + i], a);
+        vhat[i] = a;
+        acc += (double)a * (double)a;
+    }
+    if (partials) block_sum_store(acc, partials);
+}
+
 }  // namespace
 
 int vector_blocks() { return 152 * 8; }
@@ -267,6 +537,66 @@ cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaS
 cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st)
 {
     sum_partials_kernel<<<1, kFinThreads, 0, st>>>(p, n, out);
+    return cudaGetLastError();
+}
+
+int lsqr_dot_blocks() { return 152 * 2; }
+
+cudaError_t launch_lsqr_reset(KrylovScalars *, LsqrScalars *l, cudaStream_t st)
+{
+    lsqr_reset_kernel<<<1, 1, 0, st>>>(l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
+                           const float *s, float *basis, const LsqrScalars *l, double *partials,
+                           cudaStream_t st)
+{
+    const int nb = vector_blocks();
+    if (first)
+        lsqr_vx_kernel<true, false><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l, partials);
+    else if (last)
+        lsqr_vx_kernel<false, true><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l, partials);
+    else
+        lsqr_vx_kernel<false, false><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, basis, l, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
+                                      const double *pu, int nu, const double *pr, int nr,
+                                      cudaStream_t st)
+{
+    lsqr_finalize_beta_kernel<<<1, kFinThreads, 0, st>>>(k, l, init, pu, nu, pr, nr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int init,
+                                       const double *p, int n, cudaStream_t st)
+{
+    lsqr_finalize_alpha_kernel<<<1, kFinThreads, 0, st>>>(k, l, init, p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
+                             const float *vhat, const LsqrScalars *l, double *partials,
+                             cudaStream_t st)
+{
+    const dim3 grid((unsigned)lsqr_dot_blocks(), (unsigned)((nb + kDotVecs - 1) / kDotVecs));
+    lsqr_dots_kernel<<<grid, kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st)
+{
+    lsqr_fin_dots_kernel<<<nb, kFinThreads, 0, st>>>(l, partials, lsqr_dot_blocks());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
+                            const LsqrScalars *l, double *norm_partials, cudaStream_t st)
+{
+    lsqr_sub_kernel<<<vector_blocks(), kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l,
+                                                          norm_partials);
     return cudaGetLastError();
 }
 

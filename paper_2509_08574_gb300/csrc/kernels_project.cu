@@ -86,9 +86,10 @@ template <int MODE, bool NORM>
 __global__ void __launch_bounds__(256)
 fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
            const int4 *__restrict__ cells, const float *__restrict__ vol,
-           float *__restrict__ out, const float *__restrict__ b, double *__restrict__ partials,
+           float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
            int *__restrict__ nonfinite)
 {
+    if (MODE == FWD_LSQR && aux[2] != 0.f) return;  // the Krylov cycle has stopped
     int col, p;
     decode_block(G, col, p);
     const bool pair_ok = p < npairs_rows(G.nv);
@@ -148,11 +149,15 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
         float qa = sec * acca, qb = sec * accb;
         if (MODE == FWD_RESID) {
-            const float ba = b[ia];
-            const float bb = has_b ? b[ib] : 0.f;
+            const float ba = aux[ia];
+            const float bb = has_b ? aux[ib] : 0.f;
             if (!isfinite(ba) || !isfinite(bb)) atomicOr(nonfinite, 1);
             qa = ba - qa;
             qb = bb - qb;
+        } else if (MODE == FWD_LSQR) {
+            const float ka = aux[0], kb = aux[1];
+            qa = fmaf(ka, qa, -kb * out[ia]);
+            qb = has_b ? fmaf(ka, qb, -kb * out[ib]) : 0.f;
         }
         out[ia] = qa;
         if (has_b) out[ib] = qb;
@@ -280,25 +285,20 @@ int project_blocks(const ProjGeom &g)
 
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
-                           const float *b, double *partials, int *nonfinite, cudaStream_t st)
+                           const float *aux, double *partials, int *nonfinite, cudaStream_t st)
 {
     const int nb = project_blocks(g);
     if (nb <= 0) return cudaSuccess;
+#define PICCS_FWD(M, NORM) \
+    fwd_kernel<M, NORM><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, nonfinite)
     if (mode == FWD_RESID) {
-        if (partials)
-            fwd_kernel<FWD_RESID, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
-                                                            partials, nonfinite);
-        else
-            fwd_kernel<FWD_RESID, false><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
-                                                             partials, nonfinite);
+        if (partials) PICCS_FWD(FWD_RESID, true); else PICCS_FWD(FWD_RESID, false);
+    } else if (mode == FWD_LSQR) {
+        if (partials) PICCS_FWD(FWD_LSQR, true); else PICCS_FWD(FWD_LSQR, false);
     } else {
-        if (partials)
-            fwd_kernel<FWD_PLAIN, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
-                                                            partials, nonfinite);
-        else
-            fwd_kernel<FWD_PLAIN, false><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, b,
-                                                             partials, nonfinite);
+        if (partials) PICCS_FWD(FWD_PLAIN, true); else PICCS_FWD(FWD_PLAIN, false);
     }
+#undef PICCS_FWD
     return cudaGetLastError();
 }
 

@@ -175,6 +175,79 @@ reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
     if (partials) block_sum_store(acc, partials);
 }
 
+// Block sums of up to three per-thread values, one partial per block each,
+// at partials[a * gridDim.x + blockIdx.x].
+template <int NV>
+__device__ __forceinline__ void block_sums_store(const double (&v)[NV], double *partials)
+{
+    __shared__ double red[NV][kThreads / 32];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        double t = v[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += red[threadIdx.x][w];
+        partials[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// LSQR z-step fused with the regularisation part of A~^T u.  The new z at a
+// voxel is formed where it is needed (z' = ca src - cb zold, or -src in the
+// first step of a cycle), so the 7-point stencil K z' reads src and zold at
+// the neighbours and z' is written to a second buffer.
+template <bool INIT>
+__global__ void __launch_bounds__(kThreads)
+lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
+                 const float *__restrict__ zold, float *__restrict__ znew,
+                 const float *__restrict__ omega, float lam2, const float *__restrict__ c,
+                 const float *__restrict__ xp, float *__restrict__ s,
+                 const float *__restrict__ co, double *__restrict__ partials)
+{
+    float ca = -1.f, cb = 0.f, sig = 1.f;
+    if (!INIT) {
+        if (co[3] != 0.f) return;
+        ca = co[0];
+        cb = co[1];
+        sig = co[2];
+    }
+    auto zn = [&](long long j) { return INIT ? -src[j] : fmaf(ca, src[j], -cb * zold[j]); };
+    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+         i += (long long)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        unflatten(i, d.ny, d.nz, ix, iy, iz);
+        const float zi = zn(i);
+        const float w = omega[i];
+        const float gx = (ix + 1 < d.nx) ? zi - zn(i + sx) : 0.f;
+        const float gy = (iy + 1 < d.ny) ? zi - zn(i + sy) : 0.f;
+        const float gz = (iz + 1 < d.nz) ? zi - zn(i + 1) : 0.f;
+        float t = w * (gx + gy + gz);
+        if (ix >= 1) t -= omega[i - sx] * (zn(i - sx) - zi);
+        if (iy >= 1) t -= omega[i - sy] * (zn(i - sy) - zi);
+        if (iz >= 1) t -= omega[i - 1] * (zn(i - 1) - zi);
+        t = fmaf(lam2, zi, t);
+        const float ci = c[i];
+        znew[i] = zi;
+        s[i] = fmaf(sig, ci, t);
+        acc[0] += (double)(w * (gx * gx + gy * gy + gz * gz) + lam2 * zi * zi);
+        acc[1] += (double)(zi * ci);
+        if (INIT && xp) acc[2] += (double)(xp[i] * ci);  // |b_R|^2 (no prior: b_R = 0)
+    }
+    if (INIT) {
+        block_sums_store<3>(acc, partials);
+    } else {
+        const double a2[2] = {acc[0], acc[1]};
+        block_sums_store<2>(a2, partials);
+    }
+}
+
 }  // namespace
 
 int stencil_blocks(long long M)
@@ -223,6 +296,21 @@ cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, fl
     const long long M = (long long)d.nx * d.ny * d.nz;
     reg_restart_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, x, omega, lam2_piple, c, g,
                                                               s, first, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
+                             float *znew, const float *omega, float lam2_piple, const float *c,
+                             const float *xp, float *s, const float *co, double *partials,
+                             cudaStream_t st)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    if (init)
+        lsqr_ureg_kernel<true><<<stencil_blocks(M), kThreads, 0, st>>>(
+            d, M, src, zold, znew, omega, lam2_piple, c, xp, s, co, partials);
+    else
+        lsqr_ureg_kernel<false><<<stencil_blocks(M), kThreads, 0, st>>>(
+            d, M, src, zold, znew, omega, lam2_piple, c, xp, s, co, partials);
     return cudaGetLastError();
 }
 

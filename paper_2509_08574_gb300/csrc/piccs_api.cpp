@@ -46,6 +46,11 @@ struct piccs_ctx {
     double *part_fwd = nullptr, *part_vol = nullptr, *part_vec = nullptr;
     int n_part_fwd = 0, n_part_vol = 0, n_part_vec = 0;
     KrylovScalars *ks = nullptr;
+    LsqrScalars *ls = nullptr;
+    // LSQR re-orthogonalisation basis, allocated on first use
+    float *basis = nullptr;
+    int basis_cap = 0;  // vectors
+    double *part_dots = nullptr;
     int *flag = nullptr;
     double *dsum = nullptr;
 
@@ -166,6 +171,8 @@ int check_params(const piccs_params *p, char *why, size_t n)
     if (p->variant < 0 || p->variant > 3) { snprintf(why, n, "unknown variant %d", p->variant); return PICCS_EINVAL; }
     if (p->weight_rule < 0 || p->weight_rule > 1) { snprintf(why, n, "unknown weight_rule %d", p->weight_rule); return PICCS_EINVAL; }
     if (p->x0_mode < 0 || p->x0_mode > 2) { snprintf(why, n, "unknown x0_mode %d", p->x0_mode); return PICCS_EINVAL; }
+    if (p->solver < 0 || p->solver > 2) { snprintf(why, n, "unknown solver %d", p->solver); return PICCS_EINVAL; }
+    if (p->solver == PICCS_SOLVER_LSQR_REORTH && p->n_inner - 1 > kMaxBasis) { snprintf(why, n, "LSQR_REORTH needs n_inner - 1 <= %d", kMaxBasis); return PICCS_EINVAL; }
     return PICCS_OK;
 }
 
@@ -173,7 +180,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
     size_t off_cols, off_vr, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
-        off_b, off_rs, off_pf, off_pv, off_pvec, off_ks,
+        off_b, off_rs, off_pf, off_pv, off_pvec, off_ks, off_ls,
         off_flag, off_dsum, total;
     int n_pf, n_pv, n_pvec;
 };
@@ -200,9 +207,10 @@ Layout plan(const piccs_geometry *g)
     L.off_b = o; o += align256(N * sizeof(float));
     L.off_rs = o; o += align256(N * sizeof(float));
     L.off_pf = o; o += align256((size_t)L.n_pf * sizeof(double));
-    L.off_pv = o; o += align256((size_t)L.n_pv * sizeof(double));
+    L.off_pv = o; o += align256(3 * (size_t)L.n_pv * sizeof(double));  // up to 3 sums per pass
     L.off_pvec = o; o += align256((size_t)L.n_pvec * sizeof(double));
     L.off_ks = o; o += align256(sizeof(KrylovScalars));
+    L.off_ls = o; o += align256(sizeof(LsqrScalars));
     L.off_flag = o; o += align256(sizeof(int));
     L.off_dsum = o; o += align256(sizeof(double));
     L.total = o;
@@ -210,6 +218,17 @@ Layout plan(const piccs_geometry *g)
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// LSQR re-orthogonalisation: n_inner - 1 basis vectors (the last step of a
+// cycle needs none) and the Gram-Schmidt partial sums
+size_t basis_vectors(int n_inner) { return n_inner > 1 ? (size_t)(n_inner - 1) : 0; }
+
+size_t basis_bytes(const piccs_geometry *g, int n_inner)
+{
+    const size_t M = (size_t)g->nx * g->ny * g->nz;
+    return align256(basis_vectors(n_inner) * (size_t)lsqr_basis_stride((long long)M) * sizeof(float)) +
+           align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
+}
 
 }  // namespace
 
@@ -239,6 +258,8 @@ int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *pa
     if (rc != PICCS_OK) return rc;
     if (!bytes) return set_err(nullptr, PICCS_EINVAL, "bytes is NULL");
     *bytes = plan(geometry).total;
+    if (params && params->solver == PICCS_SOLVER_LSQR_REORTH)
+        *bytes += basis_bytes(geometry, params->n_inner);
     return PICCS_OK;
 }
 
@@ -307,6 +328,7 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->n_part_vol = L.n_pv;
     ctx->n_part_vec = L.n_pvec;
     ctx->ks = reinterpret_cast<KrylovScalars *>(b + L.off_ks);
+    ctx->ls = reinterpret_cast<LsqrScalars *>(b + L.off_ls);
     ctx->flag = reinterpret_cast<int *>(b + L.off_flag);
     ctx->dsum = reinterpret_cast<double *>(b + L.off_dsum);
 
@@ -325,6 +347,7 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     if (e == cudaSuccess && !hits.empty())
         e = cudaMemcpy(ctx->hits, hits.data(), hits.size() * sizeof(CellHit), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(ctx->ks, 0, sizeof(KrylovScalars));
+    if (e == cudaSuccess) e = cudaMemset(ctx->ls, 0, sizeof(LsqrScalars));
     if (e != cudaSuccess) {
         cudaFree(ctx->base);
         delete ctx;
@@ -343,6 +366,8 @@ void piccs_destroy(piccs_ctx *ctx)
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    cudaFree(ctx->basis);
+    cudaFree(ctx->part_dots);
     cudaFree(ctx->base);
     delete ctx;
 }
@@ -482,6 +507,97 @@ int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *p
 }
 
 // One IRN-PICCS reconstruction from device-resident data d_b into ctx->x.
+// Allocates the LSQR re-orthogonalisation basis on first use (synchronises).
+static int ensure_basis(piccs_ctx *ctx, int n_inner)
+{
+    const int need = (int)basis_vectors(n_inner);
+    if (need <= ctx->basis_cap && ctx->part_dots) return PICCS_OK;
+    const size_t bytes = basis_bytes(&ctx->geo, n_inner);
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
+    const size_t ldb = (size_t)lsqr_basis_stride(ctx->M);
+    const size_t held = ctx->basis ? (size_t)ctx->basis_cap * ldb * sizeof(float) : 0;
+    if (bytes > free_b + held)
+        return set_err(ctx, PICCS_ENOMEM, "LSQR basis needs %zu bytes, %zu free", bytes, free_b + held);
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->basis);
+    cudaFree(ctx->part_dots);
+    ctx->basis = nullptr;
+    ctx->part_dots = nullptr;
+    ctx->basis_cap = 0;
+    const size_t vec_bytes = (size_t)(need > 0 ? need : 1) * ldb * sizeof(float);
+    if (cudaMalloc(&ctx->basis, vec_bytes) != cudaSuccess ||
+        cudaMalloc(&ctx->part_dots, (size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->basis);
+        ctx->basis = nullptr;
+        return set_err(ctx, PICCS_ENOMEM, "cudaMalloc of the LSQR basis (%zu bytes) failed", vec_bytes);
+    }
+    ctx->basis_cap = need;
+    return PICCS_OK;
+}
+
+// One IRN cycle with LSQR as the inner solver (weights already frozen in
+// omega, c).  Buffers: uA in r, vhat in p, w in g, z alternating between t
+// and w2sq (free once c is formed), s = the regularisation part of A~^T u
+// plus, after the adjoint, A^T uA.
+static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_params *p)
+{
+    cudaStream_t st = ctx->stream;
+    const long long M = ctx->M;
+    const float l2p = lam2_piple(p);
+    const bool reorth = p->solver == PICCS_SOLVER_LSQR_REORTH;
+    const bool prior_rhs = p->variant == PICCS_VARIANT_PICCS || p->variant == PICCS_VARIANT_PIPLE;
+    LsqrScalars *ls = ctx->ls;
+    float *z[2] = {ctx->t, ctx->w2sq};
+    int cur = 0;
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st));
+    // beta_1 u_1 = b~ - A~ x: uA = b - A x, z = -x, sigma = 1
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID,
+                                                     d_b, ctx->part_fwd, &ctx->ks->nonfinite, st));
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, ctx->x, nullptr, z[cur], ctx->omega, l2p, ctx->c,
+                                                   prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
+                                                   ctx->part_vol, st));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_fwd, ctx->n_part_fwd,
+                                                               ctx->part_vol, ctx->n_part_vol, st));
+    // alpha_1 v_1 = A~^T u_1
+    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
+                                                     ctx->rs, ctx->s, st));
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr, ls,
+                                                    ctx->part_vec, st));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st));
+    for (int i = 1; i <= p->n_inner; ++i) {
+        const bool last = i == p->n_inner;
+        // beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
+        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p, ctx->r,
+                                                         FWD_LSQR, ls->fwd, ctx->part_fwd, nullptr, st));
+        LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ctx->omega, l2p,
+                                                       ctx->c, nullptr, ctx->s, ls->ureg, ctx->part_vol, st));
+        cur ^= 1;
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 0, ctx->part_fwd, ctx->n_part_fwd,
+                                                                   ctx->part_vol, ctx->n_part_vol, st));
+        // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
+        if (!last)
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
+                                                             ctx->r, ctx->rs, ctx->s, st));
+        const long long ldb = lsqr_basis_stride(M);
+        float *bv = (reorth && !last) ? ctx->basis + (size_t)(i - 1) * ldb : nullptr;
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 0, last, ctx->x, ctx->g, ctx->p, ctx->s, bv, ls,
+                                                        ctx->part_vec, st));
+        if (last) break;
+        if (reorth) {
+            for (int pass = 0; pass < 2; ++pass) {
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ls, ctx->part_dots, st));
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ls, ctx->part_dots, st));
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_sub(M, ldb, i, ctx->basis, ctx->p, ls,
+                                                                 pass == 1 ? ctx->part_vec : nullptr, st));
+            }
+        }
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 0, ctx->part_vec, ctx->n_part_vec, st));
+    }
+    return PICCS_OK;
+}
+
 static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
                                const float *d_x0)
 {
@@ -496,6 +612,22 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->x, 0, M * sizeof(float), st));
     } else {
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, d_x0, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    if (p->solver != PICCS_SOLVER_CGLS) {
+        if (p->solver == PICCS_SOLVER_LSQR_REORTH) {
+            int rc = ensure_basis(ctx, p->n_inner);
+            if (rc != PICCS_OK) return rc;
+        }
+        if (p->n_inner == 0) {  // no inner step: x stays x0; still flag NaN/Inf in b
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st));
+            return PICCS_OK;
+        }
+        for (int k = 0; k < p->n_outer; ++k) {
+            int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c);
+            if (rc == PICCS_OK) rc = enqueue_lsqr_cycle(ctx, d_b, p);
+            if (rc != PICCS_OK) return rc;
+        }
+        return PICCS_OK;
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
     LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,

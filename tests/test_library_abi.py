@@ -83,3 +83,17 @@ def test_workspace_size(pk):
     # slot) and its transpose (16 B per crossing, bounded by nx + ny - 1 per column)
     expect = 4 * (9 * M + 4 * N) + 8 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
     assert expect <= b <= expect + (16 << 20)
+
+
+def test_solver_parameter(pk):
+    g = P.c2_needle().geometry
+    base = pk.piccs_query_workspace(g)
+    assert pk.piccs_query_workspace(g, pk.make_params(solver=pk.SOLVER_LSQR, n_inner=10)) == base
+    # the re-orthogonalisation basis: n_inner - 1 image vectors (plus the
+    # Gram-Schmidt partial sums)
+    re = pk.piccs_query_workspace(g, pk.make_params(solver=pk.SOLVER_LSQR_REORTH, n_inner=10))
+    assert 9 * 4 * g.M <= re - base <= 9 * 4 * g.M + (4 << 20)
+    for bad in (dict(solver=3), dict(solver=-1), dict(solver=2, n_outer=1, n_inner=300)):
+        with pytest.raises(pk.PiccsError) as e:
+            pk.piccs_validate(g, pk.make_params(**bad))
+        assert e.value.code == pk.PICCS_EINVAL
