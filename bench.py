@@ -34,6 +34,7 @@ import phantoms as P  # noqa: E402
 METRIC = "PICCS-Krylov recon ms/scan p50 at 256^3 (90 views of 512^2, 30 its)"
 UNIT = "ms/scan"
 L2_FLUSH_BYTES = 256 << 20
+SOLVERS = {"cgls": (0, "CGLS"), "lsqr": (1, "LSQR"), "lsqr_reorth": (2, "re-orthogonalised LSQR")}
 
 
 def parse_args():
@@ -44,6 +45,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solver", choices=list(SOLVERS), default="cgls",
+                    help="inner Krylov solver (LSQR and CGLS are equivalent in exact arithmetic)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run only the projector pair on the workload (for profiler captures)")
     return ap.parse_args()
@@ -54,16 +57,20 @@ def workload():
     return scan
 
 
-def workload_config(scan):
+def workload_config(scan, solver="cgls", workspace_bytes=None):
     g = scan.geometry
+    ws = (f"workspace {workspace_bytes / 1e9:.2f} GB" if workspace_bytes
+          else "working set larger than L2")
     return {
         "workload": (f"{scan.name}: {g.nx}^3 x {g.vx:g} mm volume, {g.n_views} views over 200 deg, "
                      f"{g.nu}x{g.nv} detector x {g.du:g} mm, DSO {g.dso:g} / DSD {g.dsd:g} mm, "
-                     f"IRN-PICCS {scan.n_outer} cycles x {scan.n_inner} CGLS iterations"),
+                     f"IRN-PICCS {scan.n_outer} cycles x {scan.n_inner} "
+                     f"{SOLVERS[solver][1]} iterations"),
+        "solver": solver,
         "volume": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.nu, g.nv],
         "iterations": scan.iterations, "alpha": scan.alpha, "lambda": scan.lam, "tau": scan.tau,
         "projection_layout": "view,u,v (v fastest)",
-        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); working set ~0.9 GB",
+        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); {ws}",
         "parallelism": "replicas (one independent reconstruction per GPU)",
     }
 
@@ -252,7 +259,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(scan),
+        "config": workload_config(scan, args.solver),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -288,7 +295,8 @@ def run_ours(args):
     xp = torch.from_numpy(xp_np).cuda()
     out = torch.empty(g.vol_shape(), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner)
+    params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner,
+                            solver=SOLVERS[args.solver][0])
     torch.cuda.synchronize()
     ctx = pk.Context(g, stream=stream)
     ctx.set_prior(xp)
@@ -362,7 +370,7 @@ def run_ours(args):
         "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(scan),
+        "config": workload_config(scan, args.solver, pk.piccs_query_workspace(g, params)),
         "p50_ms": p50, "p99_ms": p99,
         "job_scans_per_s": world * args.steps / (total_ms * 1e-3),
         "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(g.N * 4),

@@ -113,9 +113,11 @@ typedef struct {
     int iterations_run;        /* inner iterations that changed x */
     int n_history;             /* entries written to gamma_history */
     double gamma_history[512]; /* ||A~^T r~||^2 at the start of each cycle and
-                                  after every inner iteration, in order (LSQR:
-                                  not after the last iteration of a cycle, whose
-                                  value would cost one more backprojection) */
+                                  after every inner iteration, in order, except
+                                  where it would cost a backprojection nothing
+                                  else needs: after the reconstruction's last
+                                  iteration (CGLS), after each cycle's last
+                                  iteration (LSQR) */
 } piccs_stats;
 
 /* Kernel accounting of a context (see piccs_profile_enable). */

@@ -81,7 +81,9 @@ struct LsqrScalars {
     double normar0;       // |A~^T r~| at the start of the cycle
     int stopped;          // the cycle has converged or a bidiagonal entry vanished
     int nbasis;           // vectors held in the re-orthogonalisation basis
-    float fwd[4];         // forward u-step: {1/alpha_i, alpha_i/beta_i, stopped, 0}
+    float fwd[8];         // forward u-step: {1/alpha_i, alpha_i/beta_i, stopped,
+                          //  theta_i/rho_{i-1}, x step not yet applied to rA,
+                          //  first step of the cycle, 0, 0}
     float ureg[4];        // z-step: {1/alpha_i, alpha_i/beta_i, new sigma, stopped}
     float vx[8];          // {1/alpha_i, theta_i/rho_{i-1}, phi_i/rho_i, 1/beta_{i+1},
                           //  beta_{i+1}, stopped, first step of the cycle, 0}
@@ -94,9 +96,7 @@ enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_LSQR = 2 };
 int project_blocks(const ProjGeom &g);
 // vr[iv] = {v, 1/v} per detector row (1e30 for v = 0)
 // mode FWD_PLAIN: out = A vol; FWD_RESID: out = aux - A vol (aux = the data b,
-// NaN/Inf in it set *nonfinite); FWD_LSQR: out = aux[0] A vol - aux[1] out, and
-// nothing when aux[2] != 0 (aux = LsqrScalars::fwd).  partials (may be null)
-// get |out|^2 per block.
+// NaN/Inf in it set *nonfinite).  partials (may be null) get |out|^2 per block.
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
                            const float *aux, double *partials, int *nonfinite, cudaStream_t st);
@@ -105,6 +105,13 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
                            float *vol, cudaStream_t st);
+
+// LSQR u-step with the data residual kept current (aux = LsqrScalars::fwd):
+// q = aux[0] A vol; U = q - aux[1] U; first step of a cycle (aux[5]): Aw = q;
+// else rA -= aux[4] Aw, Aw = q - aux[3] Aw.  Skipped when aux[2] != 0.
+cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                                const int4 *cells, const float *vol, float *U, const float *aux,
+                                float *rA, float *Aw, double *partials, cudaStream_t st);
 
 // ---- regulariser (kernels_reg.cu) ----
 struct VolDims { int nx, ny, nz; };
@@ -161,6 +168,10 @@ cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w,
 cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
                                       const double *pu, int nu, const double *pr, int nr,
                                       cudaStream_t st);
+// Start of an LSQR cycle: update (rA -= pending x step * Aw; else rA is
+// b - A x already), then U = rA; partials get |U|^2.
+cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *Aw, float *U,
+                              const LsqrScalars *l, double *partials, cudaStream_t st);
 // alpha = |vhat|, the rest of the Givens step, the stop test
 cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int init,
                                        const double *p, int n, cudaStream_t st);

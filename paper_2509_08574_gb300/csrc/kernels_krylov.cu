@@ -229,8 +229,48 @@ __global__ void lsqr_reset_kernel(LsqrScalars *l)
     l->sigma = l->sigma_next = l->bR2 = l->normar0 = 0.0;
     l->stopped = 0;
     l->nbasis = 0;
-    for (int i = 0; i < 4; ++i) l->fwd[i] = l->ureg[i] = 0.f;
-    for (int i = 0; i < 8; ++i) l->vx[i] = 0.f;
+    for (int i = 0; i < 4; ++i) l->ureg[i] = 0.f;
+    for (int i = 0; i < 8; ++i) l->fwd[i] = l->vx[i] = 0.f;
+}
+
+// rA -= pending * Aw (update; skipped when nothing is pending, so Aw may be
+// unset), U = rA, |U|^2
+__global__ void __launch_bounds__(kThreads)
+lsqr_rinit_kernel(long long N, int update, float *__restrict__ ra, const float *__restrict__ aw,
+                  float *__restrict__ u, const LsqrScalars *__restrict__ l,
+                  double *__restrict__ partials)
+{
+    const float pend = update ? l->fwd[4] : 0.f;
+    const long long n4 = N >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float4 *r4 = reinterpret_cast<float4 *>(ra);
+    const float4 *a4 = reinterpret_cast<const float4 *>(aw);
+    float4 *u4 = reinterpret_cast<float4 *>(u);
+    double acc = 0.0;
+    for (long long i = t0; i < n4; i += stride) {
+        float4 r = r4[i];
+        if (pend != 0.f) {
+            const float4 a = a4[i];
+            r.x = fmaf(-pend, a.x, r.x);
+            r.y = fmaf(-pend, a.y, r.y);
+            r.z = fmaf(-pend, a.z, r.z);
+            r.w = fmaf(-pend, a.w, r.w);
+            r4[i] = r;
+        }
+        u4[i] = r;
+        acc += (double)fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, r.w * r.w)));
+    }
+    for (long long i = (n4 << 2) + t0; i < N; i += stride) {
+        float r = ra[i];
+        if (pend != 0.f) {
+            r = fmaf(-pend, aw[i], r);
+            ra[i] = r;
+        }
+        u[i] = r;
+        acc += (double)r * (double)r;
+    }
+    block_sum_store(acc, partials);
 }
 
 template <bool FIRST, bool LAST>
@@ -316,6 +356,7 @@ lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const doub
         l->stopped = 1;
         l->vx[2] = 0.f;
         l->vx[5] = 1.f;
+        l->fwd[4] = 0.f;
         return;
     }
     const double beta = sqrt(fmax(beta2, 0.0));
@@ -327,6 +368,7 @@ lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const doub
         l->bR2 = bR2;
         l->phibar = beta;
         l->vx[2] = 0.f;
+        l->fwd[4] = 0.f;
         return;
     }
     // one Givens rotation eliminates beta_{i+1} below rhobar_i
@@ -339,6 +381,7 @@ lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const doub
     l->s = s;
     const double tx = phi / rho;
     l->vx[2] = isfinite(tx) ? (float)tx : 0.f;
+    l->fwd[4] = l->vx[2];  // applied to x by lsqr_vx, to rA by the next forward
     if (!isfinite(tx) && k->status == 0) k->status = -4;
     if (l->vx[2] != 0.f) k->iters_run += 1;
 }
@@ -381,6 +424,8 @@ lsqr_finalize_alpha_kernel(KrylovScalars *k, LsqrScalars *l, int init, const dou
     l->fwd[0] = (float)ia;
     l->fwd[1] = (float)kb;
     l->fwd[2] = fs;
+    l->fwd[3] = (float)tw;
+    l->fwd[5] = init ? 1.f : 0.f;
     l->ureg[0] = (float)ia;
     l->ureg[1] = (float)kb;
     l->ureg[2] = (float)l->sigma_next;
@@ -541,6 +586,13 @@ cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_
 }
 
 int lsqr_dot_blocks() { return 152 * 2; }
+
+cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *Aw, float *U,
+                              const LsqrScalars *l, double *partials, cudaStream_t st)
+{
+    lsqr_rinit_kernel<<<vector_blocks(), kThreads, 0, st>>>(N, update, rA, Aw, U, l, partials);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lsqr_reset(KrylovScalars *, LsqrScalars *l, cudaStream_t st)
 {

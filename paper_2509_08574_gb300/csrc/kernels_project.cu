@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256)
 fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
            const int4 *__restrict__ cells, const float *__restrict__ vol,
            float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
-           int *__restrict__ nonfinite)
+           int *__restrict__ nonfinite, float *__restrict__ ra, float *__restrict__ aw)
 {
     if (MODE == FWD_LSQR && aux[2] != 0.f) return;  // the Krylov cycle has stopped
     int col, p;
@@ -155,9 +155,30 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
             qa = ba - qa;
             qb = bb - qb;
         } else if (MODE == FWD_LSQR) {
-            const float ka = aux[0], kb = aux[1];
-            qa = fmaf(ka, qa, -kb * out[ia]);
-            qb = has_b ? fmaf(ka, qb, -kb * out[ib]) : 0.f;
+            // u-step, and A w = A v - (theta/rho) A w kept beside it so that the
+            // deferred x step can be applied to the data residual rA
+            const float ka = aux[0], kb = aux[1], tw = aux[3], pend = aux[4];
+            const bool first = aux[5] != 0.f;
+            const float sa = ka * qa, sb = ka * qb;
+            qa = fmaf(-kb, out[ia], sa);
+            if (first) {
+                aw[ia] = sa;
+            } else {
+                const float wa = aw[ia];
+                ra[ia] = fmaf(-pend, wa, ra[ia]);
+                aw[ia] = fmaf(-tw, wa, sa);
+            }
+            qb = 0.f;
+            if (has_b) {
+                qb = fmaf(-kb, out[ib], sb);
+                if (first) {
+                    aw[ib] = sb;
+                } else {
+                    const float wb = aw[ib];
+                    ra[ib] = fmaf(-pend, wb, ra[ib]);
+                    aw[ib] = fmaf(-tw, wb, sb);
+                }
+            }
         }
         out[ia] = qa;
         if (has_b) out[ib] = qb;
@@ -290,15 +311,25 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
     const int nb = project_blocks(g);
     if (nb <= 0) return cudaSuccess;
 #define PICCS_FWD(M, NORM) \
-    fwd_kernel<M, NORM><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, nonfinite)
+    fwd_kernel<M, NORM><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, \
+                                            nonfinite, nullptr, nullptr)
     if (mode == FWD_RESID) {
         if (partials) PICCS_FWD(FWD_RESID, true); else PICCS_FWD(FWD_RESID, false);
-    } else if (mode == FWD_LSQR) {
-        if (partials) PICCS_FWD(FWD_LSQR, true); else PICCS_FWD(FWD_LSQR, false);
     } else {
         if (partials) PICCS_FWD(FWD_PLAIN, true); else PICCS_FWD(FWD_PLAIN, false);
     }
 #undef PICCS_FWD
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const float2 *vr,
+                                const int4 *cells, const float *vol, float *U, const float *aux,
+                                float *rA, float *Aw, double *partials, cudaStream_t st)
+{
+    const int nb = project_blocks(g);
+    if (nb <= 0) return cudaSuccess;
+    fwd_kernel<FWD_LSQR, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux, partials,
+                                                   nullptr, rA, Aw);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ struct piccs_ctx {
     CellHit *hits = nullptr;
     float *xprior = nullptr, *x = nullptr, *p = nullptr, *s = nullptr, *g = nullptr,
           *t = nullptr, *omega = nullptr, *c = nullptr, *w2sq = nullptr;
-    float *r = nullptr, *q = nullptr, *bstage = nullptr, *rs = nullptr;
+    float *r = nullptr, *q = nullptr, *bstage = nullptr, *rs = nullptr, *aw = nullptr;
     double *part_fwd = nullptr, *part_vol = nullptr, *part_vec = nullptr;
     int n_part_fwd = 0, n_part_vol = 0, n_part_vec = 0;
     KrylovScalars *ks = nullptr;
@@ -180,7 +180,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
     size_t off_cols, off_vr, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
-        off_b, off_rs, off_pf, off_pv, off_pvec, off_ks, off_ls,
+        off_b, off_rs, off_aw, off_pf, off_pv, off_pvec, off_ks, off_ls,
         off_flag, off_dsum, total;
     int n_pf, n_pv, n_pvec;
 };
@@ -206,6 +206,7 @@ Layout plan(const piccs_geometry *g)
     L.off_q = o; o += align256(N * sizeof(float));
     L.off_b = o; o += align256(N * sizeof(float));
     L.off_rs = o; o += align256(N * sizeof(float));
+    L.off_aw = o; o += align256(N * sizeof(float));
     L.off_pf = o; o += align256((size_t)L.n_pf * sizeof(double));
     L.off_pv = o; o += align256(3 * (size_t)L.n_pv * sizeof(double));  // up to 3 sums per pass
     L.off_pvec = o; o += align256((size_t)L.n_pvec * sizeof(double));
@@ -321,6 +322,7 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->q = reinterpret_cast<float *>(b + L.off_q);
     ctx->bstage = reinterpret_cast<float *>(b + L.off_b);
     ctx->rs = reinterpret_cast<float *>(b + L.off_rs);
+    ctx->aw = reinterpret_cast<float *>(b + L.off_aw);
     ctx->part_fwd = reinterpret_cast<double *>(b + L.off_pf);
     ctx->part_vol = reinterpret_cast<double *>(b + L.off_pv);
     ctx->part_vec = reinterpret_cast<double *>(b + L.off_pvec);
@@ -538,10 +540,11 @@ static int ensure_basis(piccs_ctx *ctx, int n_inner)
 }
 
 // One IRN cycle with LSQR as the inner solver (weights already frozen in
-// omega, c).  Buffers: uA in r, vhat in p, w in g, z alternating between t
-// and w2sq (free once c is formed), s = the regularisation part of A~^T u
-// plus, after the adjoint, A^T uA.
-static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_params *p)
+// omega, c).  Buffers: uA in r, the data residual b - A x in q (kept current
+// through A w in aw, so only the first cycle projects x), vhat in p, w in g,
+// z alternating between t and w2sq (free once c is formed), s = the
+// regularisation part of A~^T u plus, after the adjoint, A^T uA.
+static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_params *p, int cycle)
 {
     cudaStream_t st = ctx->stream;
     const long long M = ctx->M;
@@ -551,14 +554,17 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     LsqrScalars *ls = ctx->ls;
     float *z[2] = {ctx->t, ctx->w2sq};
     int cur = 0;
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st));
     // beta_1 u_1 = b~ - A~ x: uA = b - A x, z = -x, sigma = 1
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID,
-                                                     d_b, ctx->part_fwd, &ctx->ks->nonfinite, st));
+    if (cycle == 0)
+        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->q,
+                                                         FWD_RESID, d_b, nullptr, &ctx->ks->nonfinite, st));
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ls,
+                                                       ctx->part_vec, st));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st));
     LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, ctx->x, nullptr, z[cur], ctx->omega, l2p, ctx->c,
                                                    prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
                                                    ctx->part_vol, st));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_fwd, ctx->n_part_fwd,
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec,
                                                                ctx->part_vol, ctx->n_part_vol, st));
     // alpha_1 v_1 = A~^T u_1
     LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
@@ -569,8 +575,8 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     for (int i = 1; i <= p->n_inner; ++i) {
         const bool last = i == p->n_inner;
         // beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
-        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p, ctx->r,
-                                                         FWD_LSQR, ls->fwd, ctx->part_fwd, nullptr, st));
+        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward_lsqr(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p,
+                                                              ctx->r, ls->fwd, ctx->q, ctx->aw, ctx->part_fwd, st));
         LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ctx->omega, l2p,
                                                        ctx->c, nullptr, ctx->s, ls->ureg, ctx->part_vol, st));
         cur ^= 1;
@@ -624,7 +630,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         }
         for (int k = 0; k < p->n_outer; ++k) {
             int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c);
-            if (rc == PICCS_OK) rc = enqueue_lsqr_cycle(ctx, d_b, p);
+            if (rc == PICCS_OK) rc = enqueue_lsqr_cycle(ctx, d_b, p, k);
             if (rc != PICCS_OK) return rc;
         }
         return PICCS_OK;
@@ -657,6 +663,9 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
                                                 ctx->part_vol, ctx->n_part_vol, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
                                           ctx->q, ctx->ks, st));
+            // after the reconstruction's last step s = A^T r + g only feeds the
+            // history, so its backprojection is skipped
+            if (k == p->n_outer - 1 && it == p->n_inner - 1) break;
             LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st));

@@ -58,6 +58,8 @@ def test_reconstruct_matches_oracle_c1(pk, c1, name, variant, alpha, lam, n_oute
         rep = ctx.report()
     assert rep.status == 0
     assert rep.iterations_run == n_outer * n_inner
+    # |A~^T r~|^2 at each cycle start and after every step but the very last
+    assert rep.n_history == n_outer * (n_inner + 1) - 1
     x0v = xp.astype(np.float64) if x0 == 0 else np.zeros(g.vol_shape())
     ref, _, _ = O.irn(g, b.astype(np.float64), xp.astype(np.float64), x0v, alpha, lam, scan.tau,
                       n_outer, n_inner, variant=variant)

@@ -79,9 +79,9 @@ def test_workspace_size(pk):
     M, N = g.M, g.N
     ncol = g.n_views * g.nu
     stride = (g.nx + g.ny + 1) // 2 * 2
-    # nine image vectors, four data vectors, the column cell table (8 B per cell
+    # nine image vectors, five data vectors, the column cell table (8 B per cell
     # slot) and its transpose (16 B per crossing, bounded by nx + ny - 1 per column)
-    expect = 4 * (9 * M + 4 * N) + 8 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
+    expect = 4 * (9 * M + 5 * N) + 8 * ncol * stride + 16 * ncol * (g.nx + g.ny - 1)
     assert expect <= b <= expect + (16 << 20)
 
 
