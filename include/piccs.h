@@ -141,6 +141,17 @@ typedef struct piccs_ctx piccs_ctx;
  * scanning procedure, repeated scans of the same patient). */
 int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_stream);
 
+/* Create a context that reconstructs `batch` scans of the same geometry
+ * together (1 <= batch <= 64): every kernel of a reconstruction step runs
+ * once for all of them, each scan in its own slot of the workspace with its
+ * own prior, Krylov scalars and stopping.  All buffers the batched calls
+ * take are the batch's arrays back to back: priors, initial and output
+ * volumes batch x M floats, projections batch x N floats.  piccs_create is
+ * batch 1.  Paper: Sec. 3 (a patient is scanned repeatedly with one geometry;
+ * scans from several procedures on one scanner share it too). */
+int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int batch,
+                         void *cuda_stream);
+
 /* Free the context and its device memory (synchronises its stream). */
 void piccs_destroy(piccs_ctx *ctx);
 
@@ -157,12 +168,17 @@ int piccs_set_stream(piccs_ctx *ctx, void *cuda_stream);
 int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
                           size_t *bytes);
 
+/* The same for a context of `batch` slots (piccs_create_batched). */
+int piccs_query_workspace_batched(const piccs_geometry *geometry, const piccs_params *params,
+                                  int batch, size_t *bytes);
+
 /* Check a geometry and parameters without creating anything (params may be
  * NULL).  Pure host computation; needs no GPU. */
 int piccs_validate(const piccs_geometry *geometry, const piccs_params *params);
 
-/* Copy the prior reconstruction x_p (M floats, device) into context-owned
- * memory and check it for NaN/Inf (PICCS_ENONFINITE).  Synchronises.
+/* Copy the prior reconstruction x_p (M floats, device; batch x M in a
+ * batched context) into context-owned memory and check it for NaN/Inf
+ * (PICCS_ENONFINITE).  Synchronises.
  * Paper: x_p, the "good initial reconstruction" of Sec. 2.1 and Sec. 3. */
 int piccs_set_prior(piccs_ctx *ctx, const float *d_xprior);
 
@@ -181,19 +197,25 @@ int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *p
 int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_params *params,
                            const float *h_x0, float *h_vol_out);
 
-/* Wait for the context's stream and describe the last reconstruction. */
+/* Wait for the context's stream and describe the last reconstruction (of
+ * slot 0 in a batched context). */
 int piccs_report(piccs_ctx *ctx, piccs_stats *out);
 
-/* Forward projection d_proj = A d_vol (Eq. 1): N floats from M floats. */
+/* The same for slot `slot` (0 <= slot < batch) of a batched context. */
+int piccs_report_slot(piccs_ctx *ctx, int slot, piccs_stats *out);
+
+/* Forward projection d_proj = A d_vol (Eq. 1): N floats from M floats (each
+ * of the batch's volumes in a batched context, one launch per volume). */
 int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj);
 
 /* Matched backprojection d_vol = A^T d_proj (same ray/voxel weights as
- * piccs_forward): M floats from N floats.  Needed by every Krylov step
+ * piccs_forward): M floats from N floats (per volume of a batched context).
+ * Needed by every Krylov step
  * (Sec. 2.3, the text after the augmented system). */
 int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol);
 
 /* The reweighting step of one IRN cycle (Eqs. 10-11): from the current
- * iterate d_x and the prior, writes per voxel
+ * iterate d_x and the prior (slot 0's in a batched context), writes per voxel
  *   d_omega = alpha^2 w1^2 + lambda^2 w2^2      (PICCS; alpha^2 w1^2 otherwise)
  *   d_c     = lambda^2 D^T W2^2 D x_p           (PICCS; lambda^2 x_p for PIPLE;
  *                                                0 for TV and CGLS)

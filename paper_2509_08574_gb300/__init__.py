@@ -80,6 +80,9 @@ def _load():
     G, P, R = C.POINTER(piccs_geometry), C.POINTER(piccs_params), C.POINTER(piccs_stats)
     sig = {
         "piccs_create": (i, [C.POINTER(vp), G, vp]),
+        "piccs_create_batched": (i, [C.POINTER(vp), G, i, vp]),
+        "piccs_query_workspace_batched": (i, [G, P, i, C.POINTER(C.c_size_t)]),
+        "piccs_report_slot": (i, [vp, i, R]),
         "piccs_destroy": (None, [vp]),
         "piccs_last_error": (C.c_char_p, [vp]),
         "piccs_set_stream": (i, [vp, vp]),
@@ -109,7 +112,8 @@ EXPORTED = ("piccs_create", "piccs_destroy", "piccs_last_error", "piccs_set_stre
             "piccs_query_workspace", "piccs_validate", "piccs_set_prior", "piccs_reconstruct",
             "piccs_reconstruct_host", "piccs_report", "piccs_forward", "piccs_adjoint",
             "piccs_reg_weights", "piccs_reg_normal", "piccs_profile_enable",
-            "piccs_profile_read", "piccs_reg_normal_noalloc")
+            "piccs_profile_read", "piccs_reg_normal_noalloc", "piccs_create_batched",
+            "piccs_query_workspace_batched", "piccs_report_slot")
 
 
 def library():
@@ -199,6 +203,21 @@ def piccs_create(geometry, stream=None) -> int:
     return h.value
 
 
+def piccs_create_batched(geometry, batch, stream=None) -> int:
+    gs = geometry if isinstance(geometry, piccs_geometry) else make_geometry(geometry)
+    h = C.c_void_p()
+    _check(_lib.piccs_create_batched(C.byref(h), C.byref(gs), int(batch), _stream_handle(stream)))
+    return h.value
+
+
+def piccs_query_workspace_batched(geometry, params, batch) -> int:
+    gs = geometry if isinstance(geometry, piccs_geometry) else make_geometry(geometry)
+    out = C.c_size_t(0)
+    _check(_lib.piccs_query_workspace_batched(C.byref(gs), C.byref(params) if params is not None
+                                              else None, int(batch), C.byref(out)))
+    return int(out.value)
+
+
 def piccs_destroy(ctx):
     _lib.piccs_destroy(ctx)
 
@@ -229,6 +248,12 @@ def piccs_reconstruct_host(ctx, h_proj, params, h_x0, h_vol_out):
 def piccs_report(ctx) -> piccs_stats:
     rep = piccs_stats()
     _check(_lib.piccs_report(ctx, C.byref(rep)), ctx)
+    return rep
+
+
+def piccs_report_slot(ctx, slot) -> piccs_stats:
+    rep = piccs_stats()
+    _check(_lib.piccs_report_slot(ctx, int(slot), C.byref(rep)), ctx)
     return rep
 
 
@@ -282,9 +307,11 @@ def piccs_profile_read(ctx) -> dict:
 
 
 class Context:
-    """Owns one piccs_ctx (one scanner geometry) on the current CUDA device."""
+    """Owns one piccs_ctx (one scanner geometry) on the current CUDA device.
+    batch > 1: that many scans of the geometry are reconstructed together;
+    volumes and projections then carry a leading batch dimension."""
 
-    def __init__(self, geometry, stream=None):
+    def __init__(self, geometry, stream=None, batch=1):
         self.gs = make_geometry(geometry)
         self.nx, self.ny, self.nz = self.gs.nx, self.gs.ny, self.gs.nz
         self.M = self.gs.nx * self.gs.ny * self.gs.nz
@@ -294,7 +321,14 @@ class Context:
         else:
             self.proj_shape = (self.gs.n_views, self.gs.nv, self.gs.nu)
         self.vol_shape = (self.gs.nx, self.gs.ny, self.gs.nz)
-        self.h = piccs_create(self.gs, stream)
+        self.batch = int(batch)
+        if self.batch > 1:
+            self.proj_shape = (self.batch,) + self.proj_shape
+            self.vol_shape = (self.batch,) + self.vol_shape
+            self.h = piccs_create_batched(self.gs, self.batch, stream)
+        else:
+            self.h = piccs_create(self.gs, stream)
+        self.BM, self.BN = self.batch * self.M, self.batch * self.N
 
     def close(self):
         if self.h:
@@ -317,15 +351,15 @@ class Context:
         piccs_set_stream(self.h, stream)
 
     def set_prior(self, xp):
-        _ptr(xp, self.M, "prior")
+        _ptr(xp, self.BM, "prior")
         piccs_set_prior(self.h, xp)
 
     def forward(self, vol, out=None):
         import torch
         if out is None:
             out = torch.empty(self.proj_shape, dtype=torch.float32, device=vol.device)
-        _ptr(vol, self.M, "volume")
-        _ptr(out, self.N, "projections")
+        _ptr(vol, self.BM, "volume")
+        _ptr(out, self.BN, "projections")
         piccs_forward(self.h, vol, out)
         return out
 
@@ -333,8 +367,8 @@ class Context:
         import torch
         if out is None:
             out = torch.empty(self.vol_shape, dtype=torch.float32, device=proj.device)
-        _ptr(proj, self.N, "projections")
-        _ptr(out, self.M, "volume")
+        _ptr(proj, self.BN, "projections")
+        _ptr(out, self.BM, "volume")
         piccs_adjoint(self.h, proj, out)
         return out
 
@@ -342,10 +376,10 @@ class Context:
         import torch
         if out is None:
             out = torch.empty(self.vol_shape, dtype=torch.float32, device=proj.device)
-        _ptr(proj, self.N, "projections")
-        _ptr(out, self.M, "volume")
+        _ptr(proj, self.BN, "projections")
+        _ptr(out, self.BM, "volume")
         if x0 is not None:
-            _ptr(x0, self.M, "x0")
+            _ptr(x0, self.BM, "x0")
         piccs_reconstruct(self.h, proj, params, x0, out)
         return out
 
@@ -353,13 +387,15 @@ class Context:
         """proj/x0/out are host tensors or arrays (pinned for full bandwidth)."""
         if out is None:
             out = np.empty(self.vol_shape, dtype=np.float32)
-        _ptr(proj, self.N, "projections")
-        _ptr(out, self.M, "volume")
+        _ptr(proj, self.BN, "projections")
+        _ptr(out, self.BM, "volume")
+        if x0 is not None:
+            _ptr(x0, self.BM, "x0")
         piccs_reconstruct_host(self.h, proj, params, x0, out)
         return out
 
-    def report(self):
-        return piccs_report(self.h)
+    def report(self, slot=0):
+        return piccs_report_slot(self.h, slot)
 
     def profile_enable(self, timing=True):
         piccs_profile_enable(self.h, timing)

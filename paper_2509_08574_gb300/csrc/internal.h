@@ -44,6 +44,26 @@ struct ProjGeom {
     int sv32;               // sv as a 32-bit stride (1 or nu)
 };
 
+// Scans of one geometry processed together ("slots", Sec. 3's repeated scans
+// batched into one launch per step): every workspace pointer of slot s is the
+// slot-0 pointer shifted by s * stride bytes; the ray tables are shared.  A
+// kernel takes its slot from blockIdx.y (the adjoint gather: blockIdx.z; the
+// one-CTA finalize kernels: blockIdx.x).  Slots{1, 0} is a single scan.
+struct Slots {
+    int n;
+    long long stride;  // bytes
+};
+
+#ifdef __CUDACC__
+template <class T>
+__device__ __forceinline__ T *slot_ptr(T *p, long long off)
+{
+    return p ? reinterpret_cast<T *>(reinterpret_cast<char *>(const_cast<void *>(
+                                         static_cast<const void *>(p))) + off)
+             : p;
+}
+#endif
+
 // Device-side Krylov scalars (FP64), read by every vector kernel so that no
 // value has to come back to the host between kernels.
 struct KrylovScalars {
@@ -99,37 +119,40 @@ int project_blocks(const ProjGeom &g);
 // NaN/Inf in it set *nonfinite).  partials (may be null) get |out|^2 per block.
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
-                           const float *aux, double *partials, int *nonfinite, cudaStream_t st);
+                           const float *aux, double *partials, int *nonfinite, cudaStream_t st,
+                           Slots sl = Slots{1, 0});
 // vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
 // N-float scratch that receives proj scaled by each ray's sec.
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st);
+                           float *vol, cudaStream_t st, Slots sl = Slots{1, 0});
 
 // LSQR u-step with the data residual kept current (aux = LsqrScalars::fwd):
 // q = aux[0] A vol; U = q - aux[1] U; first step of a cycle (aux[5]): Aw = q;
 // else rA -= aux[4] Aw, Aw = q - aux[3] Aw.  Skipped when aux[2] != 0.
 cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                                 const int4 *cells, const float *vol, float *U, const float *aux,
-                                float *rA, float *Aw, double *partials, cudaStream_t st);
+                                float *rA, float *Aw, double *partials, cudaStream_t st,
+                                Slots sl = Slots{1, 0});
 
 // ---- regulariser (kernels_reg.cu) ----
 struct VolDims { int nx, ny, nz; };
 int stencil_blocks(long long M);
 cudaError_t launch_weights(VolDims d, const float *x, const float *xp, float alpha2,
                            float lambda2, float tau2, int rule, int variant, float *omega,
-                           float *w2sq, cudaStream_t st);
+                           float *w2sq, cudaStream_t st, Slots sl = Slots{1, 0});
 cudaError_t launch_prior_rhs(VolDims d, const float *xp, const float *w2sq, float lambda2,
-                             int variant, float *c, cudaStream_t st);
+                             int variant, float *c, cudaStream_t st, Slots sl = Slots{1, 0});
 // out = D^T diag(omega) D z (+ lam2_piple z); partials (may be null) get
 // sum omega |Dz|^2 (+ lam2_piple z^2) per block.
 cudaError_t launch_reg_normal(VolDims d, const float *z, const float *omega, float lam2_piple,
-                              float *out, double *partials, cudaStream_t st);
+                              float *out, double *partials, cudaStream_t st,
+                              Slots sl = Slots{1, 0});
 // Restart of a Krylov cycle: gn = c - D^T Omega D x (- lam2_piple x);
 // first: g = gn, s = gn; else s += gn - g, g = gn, partials get s^2.
 cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, float lam2_piple,
                                const float *c, float *g, float *s, int first, double *partials,
-                               cudaStream_t st);
+                               cudaStream_t st, Slots sl = Slots{1, 0});
 
 // LSQR z-step and the regularisation part of A~^T u (see LsqrScalars):
 // init: z' = -src, sigma' = 1; else z' = co[0] src - co[1] z (co = LsqrScalars::ureg,
@@ -139,42 +162,49 @@ cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, fl
 cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
                              float *znew, const float *omega, float lam2_piple, const float *c,
                              const float *xp, float *s, const float *co, double *partials,
-                             cudaStream_t st);
+                             cudaStream_t st, Slots sl = Slots{1, 0});
 
 // ---- Krylov vector work (kernels_krylov.cu) ----
+// (Slots: see above; bstride = the per-slot stride of the LSQR basis region,
+// which also holds that slot's Gram-Schmidt partial sums after the vectors)
 int vector_blocks();
 cudaError_t launch_p_update(long long M, const float *s, float *p, const KrylovScalars *k,
-                            cudaStream_t st);
+                            cudaStream_t st, Slots sl = Slots{1, 0});
 cudaError_t launch_x_update(long long M, long long N, float *x, const float *p, float *g,
                             const float *t, float *s, float *r, const float *q,
-                            const KrylovScalars *k, cudaStream_t st);
-cudaError_t launch_norm2(long long n, const float *v, double *partials, cudaStream_t st);
+                            const KrylovScalars *k, cudaStream_t st, Slots sl = Slots{1, 0});
+cudaError_t launch_norm2(long long n, const float *v, double *partials, cudaStream_t st,
+                         Slots sl = Slots{1, 0});
 cudaError_t launch_finalize_delta(KrylovScalars *k, const double *pa, int na, const double *pb,
-                                  int nb, cudaStream_t st);
+                                  int nb, cudaStream_t st, Slots sl = Slots{1, 0});
 cudaError_t launch_finalize_gamma(KrylovScalars *k, const double *p, int n, int restart,
-                                  cudaStream_t st);
-cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st);
-cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st);
+                                  cudaStream_t st, Slots sl = Slots{1, 0});
+cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st, Slots sl = Slots{1, 0});
+cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st,
+                                   Slots sl = Slots{1, 0});
 cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st);
 // LSQR
-cudaError_t launch_lsqr_reset(KrylovScalars *k, LsqrScalars *l, cudaStream_t st);
+cudaError_t launch_lsqr_reset(KrylovScalars *k, LsqrScalars *l, cudaStream_t st,
+                              Slots sl = Slots{1, 0});
+// Start of an LSQR cycle: update (rA -= pending x step * Aw; else rA is
+// b - A x already), then U = rA; partials get |U|^2.
+cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *Aw, float *U,
+                              const LsqrScalars *l, double *partials, cudaStream_t st,
+                              Slots sl = Slots{1, 0});
 // first: vhat = s / beta_1; else v = vhat / alpha_i, w = v - tw w, x += tx w and,
 // unless last, vhat = s / beta_{i+1} - beta_{i+1} v; basis (may be null) gets v.
 // partials get |vhat|^2 (unless last).
 cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
                            const float *s, float *basis, const LsqrScalars *l, double *partials,
-                           cudaStream_t st);
+                           cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0);
 // beta = sqrt(|uA|^2 + z.Kz + 2 sigma <z,c> + sigma^2 |b_R|^2) and the Givens step
 cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
                                       const double *pu, int nu, const double *pr, int nr,
-                                      cudaStream_t st);
-// Start of an LSQR cycle: update (rA -= pending x step * Aw; else rA is
-// b - A x already), then U = rA; partials get |U|^2.
-cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *Aw, float *U,
-                              const LsqrScalars *l, double *partials, cudaStream_t st);
+                                      cudaStream_t st, Slots sl = Slots{1, 0});
 // alpha = |vhat|, the rest of the Givens step, the stop test
 cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int init,
-                                       const double *p, int n, cudaStream_t st);
+                                       const double *p, int n, cudaStream_t st,
+                                       Slots sl = Slots{1, 0});
 // Basis vector j starts at basis + j * ldb, ldb = lsqr_basis_stride(M) (a
 // multiple of 64 floats, so every vector is 256-byte aligned for float4 access).
 inline long long lsqr_basis_stride(long long M) { return (M + 63) / 64 * 64; }
@@ -184,10 +214,12 @@ inline long long lsqr_basis_stride(long long M) { return (M + 63) / 64 * 64; }
 // norm_partials (may be null) get |vhat|^2.  All skip once l->stopped.
 cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
                              const float *vhat, const LsqrScalars *l, double *partials,
-                             cudaStream_t st);
-cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st);
+                             cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0);
+cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st,
+                                 Slots sl = Slots{1, 0}, long long bstride = 0);
 cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
-                            const LsqrScalars *l, double *norm_partials, cudaStream_t st);
+                            const LsqrScalars *l, double *norm_partials, cudaStream_t st,
+                            Slots sl = Slots{1, 0}, long long bstride = 0);
 int lsqr_dot_blocks();
 
 // ---- host helpers (piccs_api.cpp) ----

@@ -22,8 +22,12 @@ constexpr int kFinThreads = 1024;
 
 __global__ void __launch_bounds__(kThreads)
 p_update_kernel(long long M, const float *__restrict__ s, float *__restrict__ p,
-                const KrylovScalars *__restrict__ k)
+                const KrylovScalars *__restrict__ k, long long sstride)
 {
+    const long long so = blockIdx.y * sstride;
+    s = slot_ptr(s, so);
+    p = slot_ptr(p, so);
+    k = slot_ptr(k, so);
     const float beta = (float)k->beta;
     const long long n4 = M >> 2;
     const float4 *s4 = reinterpret_cast<const float4 *>(s);
@@ -52,8 +56,19 @@ __global__ void __launch_bounds__(kThreads)
 x_update_kernel(long long M, long long N, float *__restrict__ x, const float *__restrict__ p,
                 float *__restrict__ g, const float *__restrict__ t, float *__restrict__ s,
                 float *__restrict__ r, const float *__restrict__ q,
-                const KrylovScalars *__restrict__ k)
+                const KrylovScalars *__restrict__ k, long long sstride)
 {
+    {
+        const long long so = blockIdx.y * sstride;
+        x = slot_ptr(x, so);
+        p = slot_ptr(p, so);
+        g = slot_ptr(g, so);
+        t = slot_ptr(t, so);
+        s = slot_ptr(s, so);
+        r = slot_ptr(r, so);
+        q = slot_ptr(q, so);
+        k = slot_ptr(k, so);
+    }
     const float a = (float)k->a;
     const long long m4 = M >> 2, n4 = N >> 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -109,8 +124,11 @@ __device__ __forceinline__ void block_sum_store(double v, double *partials)
 
 // ||v||^2: each float4 is squared and summed in FP32, then accumulated in FP64
 __global__ void __launch_bounds__(kThreads)
-norm2_kernel(long long n, const float *__restrict__ v, double *__restrict__ partials)
+norm2_kernel(long long n, const float *__restrict__ v, double *__restrict__ partials,
+             long long sstride)
 {
+    v = slot_ptr(v, blockIdx.y * sstride);
+    partials = slot_ptr(partials, blockIdx.y * sstride);
     const long long n4 = n >> 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -142,8 +160,13 @@ __device__ double cta_sum(const double *p, int n)
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-finalize_delta_kernel(KrylovScalars *k, const double *pa, int na, const double *pb, int nb)
+finalize_delta_kernel(KrylovScalars *k, const double *pa, int na, const double *pb, int nb,
+                      long long sstride)
 {
+    const long long so = blockIdx.x * sstride;  // one CTA per slot
+    k = slot_ptr(k, so);
+    pa = slot_ptr(pa, so);
+    pb = slot_ptr(pb, so);
     const double da = cta_sum(pa, na);
     const double db = (pb && nb > 0) ? cta_sum(pb, nb) : 0.0;
     if (threadIdx.x != 0) return;
@@ -163,8 +186,10 @@ finalize_delta_kernel(KrylovScalars *k, const double *pa, int na, const double *
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-finalize_gamma_kernel(KrylovScalars *k, const double *p, int n, int restart)
+finalize_gamma_kernel(KrylovScalars *k, const double *p, int n, int restart, long long sstride)
 {
+    k = slot_ptr(k, blockIdx.x * sstride);
+    p = slot_ptr(p, blockIdx.x * sstride);
     const double gnew = cta_sum(p, n);
     if (threadIdx.x != 0) return;
     if (!isfinite(gnew)) {
@@ -186,8 +211,9 @@ finalize_gamma_kernel(KrylovScalars *k, const double *p, int n, int restart)
     if (k->n_hist < 512) k->hist[k->n_hist++] = gnew;
 }
 
-__global__ void reset_scalars_kernel(KrylovScalars *k)
+__global__ void reset_scalars_kernel(KrylovScalars *k, long long sstride)
 {
+    k = slot_ptr(k, blockIdx.x * sstride);
     k->gamma = k->gamma0 = k->delta = k->a = k->beta = 0.0;
     k->status = 0;
     k->iters_run = 0;
@@ -197,8 +223,11 @@ __global__ void reset_scalars_kernel(KrylovScalars *k)
 }
 
 __global__ void __launch_bounds__(kThreads)
-count_nonfinite_kernel(long long n, const float *__restrict__ v, int *__restrict__ flag)
+count_nonfinite_kernel(long long n, const float *__restrict__ v, int *__restrict__ flag,
+                       long long sstride)
 {
+    v = slot_ptr(v, blockIdx.y * sstride);
+    flag = slot_ptr(flag, blockIdx.y * sstride);
     int bad = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -223,8 +252,9 @@ sum_partials_kernel(const double *p, int n, double *out)
 // optionally the re-orthogonalisation, and finalize_alpha (alpha_{i+1},
 // theta_{i+1}, rhobar_{i+1}, the stop test).
 
-__global__ void lsqr_reset_kernel(LsqrScalars *l)
+__global__ void lsqr_reset_kernel(LsqrScalars *l, long long sstride)
 {
+    l = slot_ptr(l, blockIdx.x * sstride);
     l->alpha = l->beta = l->rhobar = l->phibar = l->c = l->s = l->rho = 0.0;
     l->sigma = l->sigma_next = l->bR2 = l->normar0 = 0.0;
     l->stopped = 0;
@@ -238,8 +268,16 @@ __global__ void lsqr_reset_kernel(LsqrScalars *l)
 __global__ void __launch_bounds__(kThreads)
 lsqr_rinit_kernel(long long N, int update, float *__restrict__ ra, const float *__restrict__ aw,
                   float *__restrict__ u, const LsqrScalars *__restrict__ l,
-                  double *__restrict__ partials)
+                  double *__restrict__ partials, long long sstride)
 {
+    {
+        const long long so = blockIdx.y * sstride;
+        ra = slot_ptr(ra, so);
+        aw = slot_ptr(aw, so);
+        u = slot_ptr(u, so);
+        l = slot_ptr(l, so);
+        partials = slot_ptr(partials, so);
+    }
     const float pend = update ? l->fwd[4] : 0.f;
     const long long n4 = N >> 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -277,8 +315,19 @@ template <bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kThreads)
 lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
                float *__restrict__ vhat, const float *__restrict__ s, float *__restrict__ basis,
-               const LsqrScalars *__restrict__ l, double *__restrict__ partials)
+               const LsqrScalars *__restrict__ l, double *__restrict__ partials, long long sstride,
+               long long bstride)
 {
+    {
+        const long long so = blockIdx.y * sstride;
+        x = slot_ptr(x, so);
+        w = slot_ptr(w, so);
+        vhat = slot_ptr(vhat, so);
+        s = slot_ptr(s, so);
+        l = slot_ptr(l, so);
+        partials = slot_ptr(partials, so);
+        basis = slot_ptr(basis, blockIdx.y * bstride);
+    }
     const float ia = l->vx[0], tw = l->vx[1], tx = l->vx[2], ib = l->vx[3], bb = l->vx[4];
     if (!FIRST && l->vx[5] != 0.f) return;
     const bool wrestart = l->vx[6] != 0.f;  // first step of a cycle: w = v
@@ -341,8 +390,15 @@ lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
 
 __global__ void __launch_bounds__(kFinThreads)
 lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const double *pu, int nu,
-                          const double *pr, int nr)
+                          const double *pr, int nr, long long sstride)
 {
+    {
+        const long long so = blockIdx.x * sstride;  // one CTA per slot
+        k = slot_ptr(k, so);
+        l = slot_ptr(l, so);
+        pu = slot_ptr(pu, so);
+        pr = slot_ptr(pr, so);
+    }
     const double u2 = cta_sum(pu, nu);
     const double zkz = cta_sum(pr, nr);
     const double zc = cta_sum(pr + nr, nr);
@@ -387,8 +443,15 @@ lsqr_finalize_beta_kernel(KrylovScalars *k, LsqrScalars *l, int init, const doub
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-lsqr_finalize_alpha_kernel(KrylovScalars *k, LsqrScalars *l, int init, const double *p, int n)
+lsqr_finalize_alpha_kernel(KrylovScalars *k, LsqrScalars *l, int init, const double *p, int n,
+                           long long sstride)
 {
+    {
+        const long long so = blockIdx.x * sstride;
+        k = slot_ptr(k, so);
+        l = slot_ptr(l, so);
+        p = slot_ptr(p, so);
+    }
     const double a2 = cta_sum(p, n);
     if (threadIdx.x != 0) return;
     if (l->stopped) return;
@@ -443,8 +506,15 @@ constexpr int kDotVecs = 8;
 __global__ void __launch_bounds__(kThreads)
 lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
                  const float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
-                 double *__restrict__ partials)
+                 double *__restrict__ partials, long long sstride, long long bstride)
 {
+    {
+        const long long so = blockIdx.z * sstride, bo = blockIdx.z * bstride;
+        vhat = slot_ptr(vhat, so);
+        l = slot_ptr(l, so);
+        basis = slot_ptr(basis, bo);
+        partials = slot_ptr(partials, bo);
+    }
     if (l->stopped) return;
     const int j0 = blockIdx.y * kDotVecs;
     const int nj = min(kDotVecs, nb - j0);
@@ -488,8 +558,11 @@ lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ b
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-lsqr_fin_dots_kernel(LsqrScalars *l, const double *partials, int nblk)
+lsqr_fin_dots_kernel(LsqrScalars *l, const double *partials, int nblk, long long sstride,
+                     long long bstride)
 {
+    l = slot_ptr(l, blockIdx.y * sstride);
+    partials = slot_ptr(partials, blockIdx.y * bstride);
     const double h = cta_sum(partials + (long long)blockIdx.x * nblk, nblk);
     if (threadIdx.x == 0) l->h[blockIdx.x] = l->stopped ? 0.0 : h;
 }
@@ -498,8 +571,15 @@ lsqr_fin_dots_kernel(LsqrScalars *l, const double *partials, int nblk)
 __global__ void __launch_bounds__(kThreads)
 lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
                 float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
-                double *__restrict__ partials)
+                double *__restrict__ partials, long long sstride, long long bstride)
 {
+    {
+        const long long so = blockIdx.y * sstride;
+        vhat = slot_ptr(vhat, so);
+        l = slot_ptr(l, so);
+        partials = slot_ptr(partials, so);
+        basis = slot_ptr(basis, blockIdx.y * bstride);
+    }
     if (l->stopped) return;
     const long long n4 = M >> 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -533,49 +613,52 @@ lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ ba
 int vector_blocks() { return 152 * 8; }
 
 cudaError_t launch_p_update(long long M, const float *s, float *p, const KrylovScalars *k,
-                            cudaStream_t st)
+                            cudaStream_t st, Slots sl)
 {
-    p_update_kernel<<<vector_blocks(), kThreads, 0, st>>>(M, s, p, k);
+    p_update_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(M, s, p, k, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_x_update(long long M, long long N, float *x, const float *p, float *g,
                             const float *t, float *s, float *r, const float *q,
-                            const KrylovScalars *k, cudaStream_t st)
+                            const KrylovScalars *k, cudaStream_t st, Slots sl)
 {
-    x_update_kernel<<<vector_blocks(), kThreads, 0, st>>>(M, N, x, p, g, t, s, r, q, k);
+    x_update_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(M, N, x, p, g, t, s, r, q, k,
+                                                                     sl.stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_norm2(long long n, const float *v, double *partials, cudaStream_t st)
+cudaError_t launch_norm2(long long n, const float *v, double *partials, cudaStream_t st, Slots sl)
 {
-    norm2_kernel<<<vector_blocks(), kThreads, 0, st>>>(n, v, partials);
+    norm2_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(n, v, partials, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_delta(KrylovScalars *k, const double *pa, int na, const double *pb,
-                                  int nb, cudaStream_t st)
+                                  int nb, cudaStream_t st, Slots sl)
 {
-    finalize_delta_kernel<<<1, kFinThreads, 0, st>>>(k, pa, na, pb, nb);
+    finalize_delta_kernel<<<sl.n, kFinThreads, 0, st>>>(k, pa, na, pb, nb, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_gamma(KrylovScalars *k, const double *p, int n, int restart,
-                                  cudaStream_t st)
+                                  cudaStream_t st, Slots sl)
 {
-    finalize_gamma_kernel<<<1, kFinThreads, 0, st>>>(k, p, n, restart);
+    finalize_gamma_kernel<<<sl.n, kFinThreads, 0, st>>>(k, p, n, restart, sl.stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st)
+cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st, Slots sl)
 {
-    reset_scalars_kernel<<<1, 1, 0, st>>>(k);
+    reset_scalars_kernel<<<sl.n, 1, 0, st>>>(k, sl.stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st)
+cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st,
+                                   Slots sl)
 {
-    count_nonfinite_kernel<<<vector_blocks(), kThreads, 0, st>>>(n, v, flag);
+    count_nonfinite_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(n, v, flag,
+                                                                            sl.stride);
     return cudaGetLastError();
 }
 
@@ -588,67 +671,78 @@ cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_
 int lsqr_dot_blocks() { return 152 * 2; }
 
 cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *Aw, float *U,
-                              const LsqrScalars *l, double *partials, cudaStream_t st)
+                              const LsqrScalars *l, double *partials, cudaStream_t st, Slots sl)
 {
-    lsqr_rinit_kernel<<<vector_blocks(), kThreads, 0, st>>>(N, update, rA, Aw, U, l, partials);
+    lsqr_rinit_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(N, update, rA, Aw, U, l,
+                                                                       partials, sl.stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr_reset(KrylovScalars *, LsqrScalars *l, cudaStream_t st)
+cudaError_t launch_lsqr_reset(KrylovScalars *, LsqrScalars *l, cudaStream_t st, Slots sl)
 {
-    lsqr_reset_kernel<<<1, 1, 0, st>>>(l);
+    lsqr_reset_kernel<<<sl.n, 1, 0, st>>>(l, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
                            const float *s, float *basis, const LsqrScalars *l, double *partials,
-                           cudaStream_t st)
+                           cudaStream_t st, Slots sl, long long bstride)
 {
-    const int nb = vector_blocks();
+    const dim3 grid(vector_blocks(), sl.n);
     if (first)
-        lsqr_vx_kernel<true, false><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l, partials);
+        lsqr_vx_kernel<true, false><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
+                                                              partials, sl.stride, 0);
     else if (last)
-        lsqr_vx_kernel<false, true><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l, partials);
+        lsqr_vx_kernel<false, true><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
+                                                              partials, sl.stride, 0);
     else
-        lsqr_vx_kernel<false, false><<<nb, kThreads, 0, st>>>(M, x, w, vhat, s, basis, l, partials);
+        lsqr_vx_kernel<false, false><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, basis, l,
+                                                               partials, sl.stride, bstride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
                                       const double *pu, int nu, const double *pr, int nr,
-                                      cudaStream_t st)
+                                      cudaStream_t st, Slots sl)
 {
-    lsqr_finalize_beta_kernel<<<1, kFinThreads, 0, st>>>(k, l, init, pu, nu, pr, nr);
+    lsqr_finalize_beta_kernel<<<sl.n, kFinThreads, 0, st>>>(k, l, init, pu, nu, pr, nr,
+                                                            sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int init,
-                                       const double *p, int n, cudaStream_t st)
+                                       const double *p, int n, cudaStream_t st, Slots sl)
 {
-    lsqr_finalize_alpha_kernel<<<1, kFinThreads, 0, st>>>(k, l, init, p, n);
+    lsqr_finalize_alpha_kernel<<<sl.n, kFinThreads, 0, st>>>(k, l, init, p, n, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
                              const float *vhat, const LsqrScalars *l, double *partials,
-                             cudaStream_t st)
+                             cudaStream_t st, Slots sl, long long bstride)
 {
-    const dim3 grid((unsigned)lsqr_dot_blocks(), (unsigned)((nb + kDotVecs - 1) / kDotVecs));
-    lsqr_dots_kernel<<<grid, kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l, partials);
+    const dim3 grid((unsigned)lsqr_dot_blocks(), (unsigned)((nb + kDotVecs - 1) / kDotVecs),
+                    (unsigned)sl.n);
+    lsqr_dots_kernel<<<grid, kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l, partials, sl.stride,
+                                                bstride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st)
+cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st,
+                                 Slots sl, long long bstride)
 {
-    lsqr_fin_dots_kernel<<<nb, kFinThreads, 0, st>>>(l, partials, lsqr_dot_blocks());
+    lsqr_fin_dots_kernel<<<dim3(nb, sl.n), kFinThreads, 0, st>>>(l, partials, lsqr_dot_blocks(),
+                                                                 sl.stride, bstride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
-                            const LsqrScalars *l, double *norm_partials, cudaStream_t st)
+                            const LsqrScalars *l, double *norm_partials, cudaStream_t st, Slots sl,
+                            long long bstride)
 {
-    lsqr_sub_kernel<<<vector_blocks(), kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l,
-                                                          norm_partials);
+    lsqr_sub_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l,
+                                                                     norm_partials, sl.stride,
+                                                                     bstride);
     return cudaGetLastError();
 }
 

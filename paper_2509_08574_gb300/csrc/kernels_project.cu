@@ -87,8 +87,19 @@ __global__ void __launch_bounds__(256)
 fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
            const int4 *__restrict__ cells, const float *__restrict__ vol,
            float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
-           int *__restrict__ nonfinite, float *__restrict__ ra, float *__restrict__ aw)
+           int *__restrict__ nonfinite, float *__restrict__ ra, float *__restrict__ aw,
+           long long sstride)
 {
+    if (sstride) {  // slot blockIdx.y of a batch
+        const long long so = blockIdx.y * sstride;
+        vol = slot_ptr(vol, so);
+        out = slot_ptr(out, so);
+        aux = slot_ptr(aux, so);
+        partials = slot_ptr(partials, so);
+        nonfinite = slot_ptr(nonfinite, so);
+        ra = slot_ptr(ra, so);
+        aw = slot_ptr(aw, so);
+    }
     if (MODE == FWD_LSQR && aux[2] != 0.f) return;  // the Krylov cycle has stopped
     int col, p;
     decode_block(G, col, p);
@@ -202,8 +213,10 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
 // rs = proj * sec, per ray (the adjoint's gather then needs no square root)
 __global__ void __launch_bounds__(256)
 scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-                  const float *__restrict__ proj, float *__restrict__ rs)
+                  const float *__restrict__ proj, float *__restrict__ rs, long long sstride)
 {
+    proj = slot_ptr(proj, blockIdx.y * sstride);
+    rs = slot_ptr(rs, blockIdx.y * sstride);
     int col, p;
     decode_block(G, col, p);
     if (p >= npairs_rows(G.nv)) return;
@@ -227,8 +240,10 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 __global__ void __launch_bounds__(kGatherThreads)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
-                  const float *__restrict__ rs, float *__restrict__ vol)
+                  const float *__restrict__ rs, float *__restrict__ vol, long long sstride)
 {
+    rs = slot_ptr(rs, blockIdx.z * sstride);
+    vol = slot_ptr(vol, blockIdx.z * sstride);
     constexpr int L = kLayersPerThread;
     const int cell = blockIdx.x;
     const int pb = blockIdx.y * kGatherThreads * L + threadIdx.x;
@@ -306,13 +321,15 @@ int project_blocks(const ProjGeom &g)
 
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
-                           const float *aux, double *partials, int *nonfinite, cudaStream_t st)
+                           const float *aux, double *partials, int *nonfinite, cudaStream_t st,
+                           Slots sl)
 {
     const int nb = project_blocks(g);
-    if (nb <= 0) return cudaSuccess;
+    if (nb <= 0 || sl.n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)nb, (unsigned)sl.n);
 #define PICCS_FWD(M, NORM) \
-    fwd_kernel<M, NORM><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, \
-                                            nonfinite, nullptr, nullptr)
+    fwd_kernel<M, NORM><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, \
+                                              nonfinite, nullptr, nullptr, sl.stride)
     if (mode == FWD_RESID) {
         if (partials) PICCS_FWD(FWD_RESID, true); else PICCS_FWD(FWD_RESID, false);
     } else {
@@ -324,26 +341,30 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
 
 cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                                 const int4 *cells, const float *vol, float *U, const float *aux,
-                                float *rA, float *Aw, double *partials, cudaStream_t st)
+                                float *rA, float *Aw, double *partials, cudaStream_t st, Slots sl)
 {
     const int nb = project_blocks(g);
-    if (nb <= 0) return cudaSuccess;
-    fwd_kernel<FWD_LSQR, true><<<nb, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux, partials,
-                                                   nullptr, rA, Aw);
+    if (nb <= 0 || sl.n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)nb, (unsigned)sl.n);
+    fwd_kernel<FWD_LSQR, true><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux, partials,
+                                                     nullptr, rA, Aw, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st)
+                           float *vol, cudaStream_t st, Slots sl)
 {
     const int nb = project_blocks(g);
-    if (nb <= 0) return cudaSuccess;
-    scale_rays_kernel<<<nb, 256, 0, st>>>(g, cols, vr, proj, rs);
+    if (nb <= 0 || sl.n <= 0) return cudaSuccess;
+    scale_rays_kernel<<<dim3((unsigned)nb, (unsigned)sl.n), 256, 0, st>>>(g, cols, vr, proj, rs,
+                                                                          sl.stride);
     const int per_cta = kGatherThreads * kLayersPerThread;  // layer pairs per CTA
     const int nlp = (g.nz + 1) >> 1;
-    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((nlp + per_cta - 1) / per_cta));
-    adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol);
+    const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((nlp + per_cta - 1) / per_cta),
+                    (unsigned)sl.n);
+    adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol,
+                                                       sl.stride);
     return cudaGetLastError();
 }
 

@@ -44,8 +44,13 @@ __device__ __forceinline__ float weight_sq(float n2, float tau2, int rule)
 __global__ void __launch_bounds__(kThreads)
 weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float *__restrict__ xp,
                float alpha2, float lambda2, float tau2, int rule, int variant,
-               float *__restrict__ omega, float *__restrict__ w2sq)
+               float *__restrict__ omega, float *__restrict__ w2sq, long long sstride)
 {
+    const long long so = blockIdx.y * sstride;
+    x = slot_ptr(x, so);
+    xp = slot_ptr(xp, so);
+    omega = slot_ptr(omega, so);
+    w2sq = slot_ptr(w2sq, so);
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x) {
@@ -73,8 +78,13 @@ weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float 
 // c = lambda^2 D^T W2^2 D x_p (PICCS), lambda^2 x_p (PIPLE), 0 otherwise
 __global__ void __launch_bounds__(kThreads)
 prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
-                 const float *__restrict__ w2sq, float lambda2, int variant, float *__restrict__ c)
+                 const float *__restrict__ w2sq, float lambda2, int variant, float *__restrict__ c,
+                 long long sstride)
 {
+    const long long so = blockIdx.y * sstride;
+    xp = slot_ptr(xp, so);
+    w2sq = slot_ptr(w2sq, so);
+    c = slot_ptr(c, so);
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x) {
@@ -139,8 +149,13 @@ template <bool NORM>
 __global__ void __launch_bounds__(kThreads)
 reg_normal_kernel(VolDims d, long long M, const float *__restrict__ z,
                   const float *__restrict__ omega, float lam2, float *__restrict__ out,
-                  double *__restrict__ partials)
+                  double *__restrict__ partials, long long sstride)
 {
+    const long long so = blockIdx.y * sstride;
+    z = slot_ptr(z, so);
+    omega = slot_ptr(omega, so);
+    out = slot_ptr(out, so);
+    partials = slot_ptr(partials, so);
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x) {
@@ -155,8 +170,15 @@ __global__ void __launch_bounds__(kThreads)
 reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
                    const float *__restrict__ omega, float lam2, const float *__restrict__ c,
                    float *__restrict__ g, float *__restrict__ s, int first,
-                   double *__restrict__ partials)
+                   double *__restrict__ partials, long long sstride)
 {
+    const long long so = blockIdx.y * sstride;
+    x = slot_ptr(x, so);
+    omega = slot_ptr(omega, so);
+    c = slot_ptr(c, so);
+    g = slot_ptr(g, so);
+    s = slot_ptr(s, so);
+    partials = slot_ptr(partials, so);
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
          i += (long long)gridDim.x * blockDim.x) {
@@ -207,8 +229,20 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
                  const float *__restrict__ zold, float *__restrict__ znew,
                  const float *__restrict__ omega, float lam2, const float *__restrict__ c,
                  const float *__restrict__ xp, float *__restrict__ s,
-                 const float *__restrict__ co, double *__restrict__ partials)
+                 const float *__restrict__ co, double *__restrict__ partials, long long sstride)
 {
+    {
+        const long long so = blockIdx.y * sstride;
+        src = slot_ptr(src, so);
+        zold = slot_ptr(zold, so);
+        znew = slot_ptr(znew, so);
+        omega = slot_ptr(omega, so);
+        c = slot_ptr(c, so);
+        xp = slot_ptr(xp, so);
+        s = slot_ptr(s, so);
+        co = slot_ptr(co, so);
+        partials = slot_ptr(partials, so);
+    }
     float ca = -1.f, cb = 0.f, sig = 1.f;
     if (!INIT) {
         if (co[3] != 0.f) return;
@@ -260,57 +294,60 @@ int stencil_blocks(long long M)
 
 cudaError_t launch_weights(VolDims d, const float *x, const float *xp, float alpha2,
                            float lambda2, float tau2, int rule, int variant, float *omega,
-                           float *w2sq, cudaStream_t st)
+                           float *w2sq, cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
-    weights_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, x, xp, alpha2, lambda2, tau2,
-                                                          rule, variant, omega, w2sq);
+    weights_kernel<<<dim3(stencil_blocks(M), sl.n), kThreads, 0, st>>>(
+        d, M, x, xp, alpha2, lambda2, tau2, rule, variant, omega, w2sq, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prior_rhs(VolDims d, const float *xp, const float *w2sq, float lambda2,
-                             int variant, float *c, cudaStream_t st)
+                             int variant, float *c, cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
-    prior_rhs_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, xp, w2sq, lambda2, variant, c);
+    prior_rhs_kernel<<<dim3(stencil_blocks(M), sl.n), kThreads, 0, st>>>(d, M, xp, w2sq, lambda2,
+                                                                        variant, c, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reg_normal(VolDims d, const float *z, const float *omega, float lam2_piple,
-                              float *out, double *partials, cudaStream_t st)
+                              float *out, double *partials, cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
+    const dim3 grid(stencil_blocks(M), sl.n);
     if (partials)
-        reg_normal_kernel<true><<<stencil_blocks(M), kThreads, 0, st>>>(d, M, z, omega,
-                                                                       lam2_piple, out, partials);
+        reg_normal_kernel<true><<<grid, kThreads, 0, st>>>(d, M, z, omega, lam2_piple, out,
+                                                           partials, sl.stride);
     else
-        reg_normal_kernel<false><<<stencil_blocks(M), kThreads, 0, st>>>(d, M, z, omega,
-                                                                        lam2_piple, out, partials);
+        reg_normal_kernel<false><<<grid, kThreads, 0, st>>>(d, M, z, omega, lam2_piple, out,
+                                                            partials, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, float lam2_piple,
                                const float *c, float *g, float *s, int first, double *partials,
-                               cudaStream_t st)
+                               cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
-    reg_restart_kernel<<<stencil_blocks(M), kThreads, 0, st>>>(d, M, x, omega, lam2_piple, c, g,
-                                                              s, first, partials);
+    reg_restart_kernel<<<dim3(stencil_blocks(M), sl.n), kThreads, 0, st>>>(
+        d, M, x, omega, lam2_piple, c, g, s, first, partials, sl.stride);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
                              float *znew, const float *omega, float lam2_piple, const float *c,
                              const float *xp, float *s, const float *co, double *partials,
-                             cudaStream_t st)
+                             cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
+    const dim3 grid(stencil_blocks(M), sl.n);
     if (init)
-        lsqr_ureg_kernel<true><<<stencil_blocks(M), kThreads, 0, st>>>(
-            d, M, src, zold, znew, omega, lam2_piple, c, xp, s, co, partials);
+        lsqr_ureg_kernel<true><<<grid, kThreads, 0, st>>>(d, M, src, zold, znew, omega, lam2_piple,
+                                                          c, xp, s, co, partials, sl.stride);
     else
-        lsqr_ureg_kernel<false><<<stencil_blocks(M), kThreads, 0, st>>>(
-            d, M, src, zold, znew, omega, lam2_piple, c, xp, s, co, partials);
+        lsqr_ureg_kernel<false><<<grid, kThreads, 0, st>>>(d, M, src, zold, znew, omega, lam2_piple,
+                                                           c, xp, s, co, partials, sl.stride);
     return cudaGetLastError();
 }
 

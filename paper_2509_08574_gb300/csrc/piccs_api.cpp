@@ -27,6 +27,8 @@ struct piccs_ctx {
     ProjGeom pg;
     VolDims vd;
     long long M = 0, N = 0;
+    int nslot = 1;              // scans per batch (same geometry)
+    size_t slot_bytes = 0;      // stride between the slots' workspaces
     cudaStream_t stream = nullptr;
     int device = 0;
     bool has_prior = false;
@@ -47,10 +49,12 @@ struct piccs_ctx {
     int n_part_fwd = 0, n_part_vol = 0, n_part_vec = 0;
     KrylovScalars *ks = nullptr;
     LsqrScalars *ls = nullptr;
-    // LSQR re-orthogonalisation basis, allocated on first use
+    // LSQR re-orthogonalisation basis, allocated on first use: per slot the
+    // vectors, then the Gram-Schmidt partial sums, basis_bytes apart
     float *basis = nullptr;
     int basis_cap = 0;  // vectors
     double *part_dots = nullptr;
+    size_t basis_stride = 0;
     int *flag = nullptr;
     double *dsum = nullptr;
 
@@ -128,6 +132,9 @@ struct Launch {
     }
 };
 
+// all slots of the context in one launch
+#define SL(ctx) Slots{(ctx)->nslot, (long long)(ctx)->slot_bytes}
+
 #define LAUNCH(ctx, kind, call)                          \
     do {                                                 \
         Launch l_((ctx), (kind));                        \
@@ -178,14 +185,18 @@ int check_params(const piccs_params *p, char *why, size_t n)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Workspace: the ray tables (shared by all slots), then one equal-sized
+// region per slot holding that scan's vectors, partial sums and scalars.
 struct Layout {
-    size_t off_cols, off_vr, off_cells, off_hitptr, off_hits, off_img[9], off_r, off_q,
-        off_b, off_rs, off_aw, off_pf, off_pv, off_pvec, off_ks, off_ls,
-        off_flag, off_dsum, total;
+    size_t off_cols, off_vr, off_cells, off_hitptr, off_hits, off_slot0;
+    // within a slot
+    size_t off_img[9], off_r, off_q, off_b, off_rs, off_aw, off_pf, off_pv, off_pvec, off_ks,
+        off_ls, off_flag, off_dsum, slot_bytes;
+    size_t total;
     int n_pf, n_pv, n_pvec;
 };
 
-Layout plan(const piccs_geometry *g)
+Layout plan(const piccs_geometry *g, int nslot = 1)
 {
     Layout L{};
     const size_t M = (size_t)g->nx * g->ny * g->nz;
@@ -201,34 +212,51 @@ Layout plan(const piccs_geometry *g)
     L.off_cells = o; o += align256((size_t)g->n_views * g->nu * cell_stride(g) * 2 * sizeof(int));
     L.off_hitptr = o; o += align256(((size_t)g->nx * g->ny + 1) * sizeof(int));
     L.off_hits = o; o += align256(hit_bound(g) * sizeof(CellHit));
-    for (int i = 0; i < 9; ++i) { L.off_img[i] = o; o += align256(M * sizeof(float)); }
-    L.off_r = o; o += align256(N * sizeof(float));
-    L.off_q = o; o += align256(N * sizeof(float));
-    L.off_b = o; o += align256(N * sizeof(float));
-    L.off_rs = o; o += align256(N * sizeof(float));
-    L.off_aw = o; o += align256(N * sizeof(float));
-    L.off_pf = o; o += align256((size_t)L.n_pf * sizeof(double));
-    L.off_pv = o; o += align256(3 * (size_t)L.n_pv * sizeof(double));  // up to 3 sums per pass
-    L.off_pvec = o; o += align256((size_t)L.n_pvec * sizeof(double));
-    L.off_ks = o; o += align256(sizeof(KrylovScalars));
-    L.off_ls = o; o += align256(sizeof(LsqrScalars));
-    L.off_flag = o; o += align256(sizeof(int));
-    L.off_dsum = o; o += align256(sizeof(double));
-    L.total = o;
+    L.off_slot0 = o;
+    size_t q = 0;
+    for (int i = 0; i < 9; ++i) { L.off_img[i] = q; q += align256(M * sizeof(float)); }
+    L.off_r = q; q += align256(N * sizeof(float));
+    L.off_q = q; q += align256(N * sizeof(float));
+    L.off_b = q; q += align256(N * sizeof(float));
+    L.off_rs = q; q += align256(N * sizeof(float));
+    L.off_aw = q; q += align256(N * sizeof(float));
+    L.off_pf = q; q += align256((size_t)L.n_pf * sizeof(double));
+    L.off_pv = q; q += align256(3 * (size_t)L.n_pv * sizeof(double));  // up to 3 sums per pass
+    L.off_pvec = q; q += align256((size_t)L.n_pvec * sizeof(double));
+    L.off_ks = q; q += align256(sizeof(KrylovScalars));
+    L.off_ls = q; q += align256(sizeof(LsqrScalars));
+    L.off_flag = q; q += align256(sizeof(int));
+    L.off_dsum = q; q += align256(sizeof(double));
+    L.slot_bytes = q;
+    L.total = o + (size_t)nslot * q;
     return L;
 }
 
+constexpr int kMaxSlots = 64;
+
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <class T>
+T *slot_at(T *p, const piccs_ctx *ctx, int s)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(p) + (size_t)s * ctx->slot_bytes);
+}
 
 // LSQR re-orthogonalisation: n_inner - 1 basis vectors (the last step of a
 // cycle needs none) and the Gram-Schmidt partial sums
 size_t basis_vectors(int n_inner) { return n_inner > 1 ? (size_t)(n_inner - 1) : 0; }
 
-size_t basis_bytes(const piccs_geometry *g, int n_inner)
+size_t basis_vec_bytes(const piccs_geometry *g, int n_inner)
 {
     const size_t M = (size_t)g->nx * g->ny * g->nz;
-    return align256(basis_vectors(n_inner) * (size_t)lsqr_basis_stride((long long)M) * sizeof(float)) +
-           align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
+    const size_t nv = basis_vectors(n_inner) > 0 ? basis_vectors(n_inner) : 1;
+    return align256(nv * (size_t)lsqr_basis_stride((long long)M) * sizeof(float));
+}
+
+// per slot: the vectors, then the Gram-Schmidt partial sums
+size_t basis_bytes(const piccs_geometry *g, int n_inner)
+{
+    return basis_vec_bytes(g, n_inner) + align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
 }
 
 }  // namespace
@@ -252,25 +280,39 @@ int piccs_validate(const piccs_geometry *geometry, const piccs_params *params)
     return PICCS_OK;
 }
 
-int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
-                          size_t *bytes)
+int piccs_query_workspace_batched(const piccs_geometry *geometry, const piccs_params *params,
+                                  int batch, size_t *bytes)
 {
     int rc = piccs_validate(geometry, params);
     if (rc != PICCS_OK) return rc;
     if (!bytes) return set_err(nullptr, PICCS_EINVAL, "bytes is NULL");
-    *bytes = plan(geometry).total;
+    if (batch < 1 || batch > kMaxSlots) return set_err(nullptr, PICCS_EINVAL, "batch must be in [1, %d]", kMaxSlots);
+    *bytes = plan(geometry, batch).total;
     if (params && params->solver == PICCS_SOLVER_LSQR_REORTH)
-        *bytes += basis_bytes(geometry, params->n_inner);
+        *bytes += (size_t)batch * basis_bytes(geometry, params->n_inner);
     return PICCS_OK;
 }
 
+int piccs_query_workspace(const piccs_geometry *geometry, const piccs_params *params,
+                          size_t *bytes)
+{
+    return piccs_query_workspace_batched(geometry, params, 1, bytes);
+}
+
 int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_stream)
+{
+    return piccs_create_batched(out, geometry, 1, cuda_stream);
+}
+
+int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int batch,
+                         void *cuda_stream)
 {
     if (!out) return set_err(nullptr, PICCS_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = piccs_validate(geometry, nullptr);
     if (rc != PICCS_OK) return rc;
-    const Layout L = plan(geometry);
+    if (batch < 1 || batch > kMaxSlots) return set_err(nullptr, PICCS_EINVAL, "batch must be in [1, %d]", kMaxSlots);
+    const Layout L = plan(geometry, batch);
 
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
@@ -315,6 +357,9 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
     ctx->cells = reinterpret_cast<int4 *>(b + L.off_cells);
     ctx->hit_ptr = reinterpret_cast<int *>(b + L.off_hitptr);
     ctx->hits = reinterpret_cast<CellHit *>(b + L.off_hits);
+    ctx->nslot = batch;
+    ctx->slot_bytes = L.slot_bytes;
+    b += L.off_slot0;  // slot 0; slot s is s * slot_bytes further
     float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
                       &ctx->t, &ctx->omega, &ctx->c, &ctx->w2sq};
     for (int i = 0; i < 9; ++i) *img[i] = reinterpret_cast<float *>(b + L.off_img[i]);
@@ -348,8 +393,11 @@ int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_str
         e = cudaMemcpy(ctx->hit_ptr, hit_ptr.data(), hit_ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hits.empty())
         e = cudaMemcpy(ctx->hits, hits.data(), hits.size() * sizeof(CellHit), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(ctx->ks, 0, sizeof(KrylovScalars));
-    if (e == cudaSuccess) e = cudaMemset(ctx->ls, 0, sizeof(LsqrScalars));
+    for (int sl = 0; sl < batch && e == cudaSuccess; ++sl) {
+        e = cudaMemset(reinterpret_cast<char *>(ctx->ks) + sl * L.slot_bytes, 0, sizeof(KrylovScalars));
+        if (e == cudaSuccess)
+            e = cudaMemset(reinterpret_cast<char *>(ctx->ls) + sl * L.slot_bytes, 0, sizeof(LsqrScalars));
+    }
     if (e != cudaSuccess) {
         cudaFree(ctx->base);
         delete ctx;
@@ -369,7 +417,6 @@ void piccs_destroy(piccs_ctx *ctx)
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     cudaFree(ctx->basis);
-    cudaFree(ctx->part_dots);
     cudaFree(ctx->base);
     delete ctx;
 }
@@ -422,17 +469,21 @@ int piccs_set_prior(piccs_ctx *ctx, const float *d_xprior)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_xprior) return set_err(ctx, PICCS_EINVAL, "d_xprior is NULL");
-    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->xprior, d_xprior, ctx->M * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
-    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(ctx->M, ctx->xprior, ctx->flag, ctx->stream));
-    int bad = 0;
-    CUDA_TRY(ctx, cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    const int B = ctx->nslot;
+    const size_t vb = ctx->M * sizeof(float);
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->xprior, ctx->slot_bytes, d_xprior, vb, vb, B,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaMemset2DAsync(ctx->flag, ctx->slot_bytes, 0, sizeof(int), B, ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(ctx->M, ctx->xprior, ctx->flag, ctx->stream, SL(ctx)));
+    std::vector<int> bad(B, 0);
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(bad.data(), sizeof(int), ctx->flag, ctx->slot_bytes, sizeof(int), B,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    if (bad) {
-        ctx->has_prior = false;
-        return set_err(ctx, PICCS_ENONFINITE, "prior volume holds NaN or Inf");
-    }
+    for (int i = 0; i < B; ++i)
+        if (bad[i]) {
+            ctx->has_prior = false;
+            return set_err(ctx, PICCS_ENONFINITE, "prior volume %d holds NaN or Inf", i);
+        }
     ctx->has_prior = true;
     return PICCS_OK;
 }
@@ -441,8 +492,10 @@ int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, d_vol, d_proj, FWD_PLAIN, nullptr,
-                                 nullptr, nullptr, ctx->stream));
+    for (int b = 0; b < ctx->nslot; ++b)
+        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, d_vol + b * ctx->M,
+                                                         d_proj + b * ctx->N, FWD_PLAIN, nullptr, nullptr, nullptr,
+                                                         ctx->stream));
     return PICCS_OK;
 }
 
@@ -450,8 +503,11 @@ int piccs_adjoint(piccs_ctx *ctx, const float *d_proj, float *d_vol)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_vol || !d_proj) return set_err(ctx, PICCS_EINVAL, "NULL buffer");
-    CUDA_TRY(ctx, cudaMemsetAsync(d_vol, 0, ctx->M * sizeof(float), ctx->stream));
-    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, d_proj, ctx->rs, d_vol, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(d_vol, 0, ctx->nslot * ctx->M * sizeof(float), ctx->stream));
+    for (int b = 0; b < ctx->nslot; ++b)
+        LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
+                                                         d_proj + b * ctx->N, ctx->rs, d_vol + b * ctx->M,
+                                                         ctx->stream));
     return PICCS_OK;
 }
 
@@ -461,13 +517,13 @@ static float lam2_piple(const piccs_params *p)
 }
 
 static int enqueue_weights(piccs_ctx *ctx, const float *d_x, const piccs_params *p, float *omega,
-                           float *c)
+                           float *c, Slots sl)
 {
     const float a2 = p->alpha * p->alpha, l2 = p->lambda * p->lambda;
     const float tau2 = p->tau * p->tau;
     LAUNCH(ctx, PICCS_KERNEL_REG, launch_weights(ctx->vd, d_x, ctx->xprior, a2, l2, tau2, p->weight_rule,
-                                 p->variant, omega, ctx->w2sq, ctx->stream));
-    LAUNCH(ctx, PICCS_KERNEL_REG, launch_prior_rhs(ctx->vd, ctx->xprior, ctx->w2sq, l2, p->variant, c, ctx->stream));
+                                 p->variant, omega, ctx->w2sq, ctx->stream, sl));
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_prior_rhs(ctx->vd, ctx->xprior, ctx->w2sq, l2, p->variant, c, ctx->stream, sl));
     return PICCS_OK;
 }
 
@@ -487,7 +543,7 @@ int piccs_reg_weights(piccs_ctx *ctx, const float *d_x, const piccs_params *para
     if ((params->variant == PICCS_VARIANT_PICCS || params->variant == PICCS_VARIANT_PIPLE) &&
         !ctx->has_prior)
         return set_err(ctx, PICCS_EINVAL, "prior not set");
-    return enqueue_weights(ctx, d_x, params, d_omega, d_c);
+    return enqueue_weights(ctx, d_x, params, d_omega, d_c, Slots{1, 0});
 }
 
 int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *params,
@@ -513,28 +569,27 @@ int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *p
 static int ensure_basis(piccs_ctx *ctx, int n_inner)
 {
     const int need = (int)basis_vectors(n_inner);
-    if (need <= ctx->basis_cap && ctx->part_dots) return PICCS_OK;
-    const size_t bytes = basis_bytes(&ctx->geo, n_inner);
+    if (ctx->basis && need <= ctx->basis_cap) return PICCS_OK;
+    const size_t per_slot = basis_bytes(&ctx->geo, n_inner);
+    const size_t bytes = per_slot * ctx->nslot;
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
-    const size_t ldb = (size_t)lsqr_basis_stride(ctx->M);
-    const size_t held = ctx->basis ? (size_t)ctx->basis_cap * ldb * sizeof(float) : 0;
+    const size_t held = ctx->basis ? ctx->basis_stride * ctx->nslot : 0;
     if (bytes > free_b + held)
         return set_err(ctx, PICCS_ENOMEM, "LSQR basis needs %zu bytes, %zu free", bytes, free_b + held);
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(ctx->basis);
-    cudaFree(ctx->part_dots);
     ctx->basis = nullptr;
     ctx->part_dots = nullptr;
     ctx->basis_cap = 0;
-    const size_t vec_bytes = (size_t)(need > 0 ? need : 1) * ldb * sizeof(float);
-    if (cudaMalloc(&ctx->basis, vec_bytes) != cudaSuccess ||
-        cudaMalloc(&ctx->part_dots, (size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double)) != cudaSuccess) {
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(ctx->basis);
-        ctx->basis = nullptr;
-        return set_err(ctx, PICCS_ENOMEM, "cudaMalloc of the LSQR basis (%zu bytes) failed", vec_bytes);
+        return set_err(ctx, PICCS_ENOMEM, "cudaMalloc of the LSQR basis (%zu bytes) failed", bytes);
     }
+    ctx->basis = static_cast<float *>(mem);
+    ctx->part_dots = reinterpret_cast<double *>(static_cast<char *>(mem) + basis_vec_bytes(&ctx->geo, n_inner));
+    ctx->basis_stride = per_slot;
     ctx->basis_cap = need;
     return PICCS_OK;
 }
@@ -557,67 +612,73 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     // beta_1 u_1 = b~ - A~ x: uA = b - A x, z = -x, sigma = 1
     if (cycle == 0)
         LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->q,
-                                                         FWD_RESID, d_b, nullptr, &ctx->ks->nonfinite, st));
+                                                         FWD_RESID, d_b, nullptr, &ctx->ks->nonfinite, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ls,
-                                                       ctx->part_vec, st));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st));
+                                                       ctx->part_vec, st, SL(ctx)));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, ctx->x, nullptr, z[cur], ctx->omega, l2p, ctx->c,
                                                    prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
-                                                   ctx->part_vol, st));
+                                                   ctx->part_vol, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec,
-                                                               ctx->part_vol, ctx->n_part_vol, st));
+                                                               ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
     // alpha_1 v_1 = A~^T u_1
     LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
-                                                     ctx->rs, ctx->s, st));
+                                                     ctx->rs, ctx->s, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr, ls,
-                                                    ctx->part_vec, st));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st));
+                                                    ctx->part_vec, st, SL(ctx)));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
     for (int i = 1; i <= p->n_inner; ++i) {
         const bool last = i == p->n_inner;
         // beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
         LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward_lsqr(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p,
-                                                              ctx->r, ls->fwd, ctx->q, ctx->aw, ctx->part_fwd, st));
+                                                              ctx->r, ls->fwd, ctx->q, ctx->aw, ctx->part_fwd, st, SL(ctx)));
         LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ctx->omega, l2p,
-                                                       ctx->c, nullptr, ctx->s, ls->ureg, ctx->part_vol, st));
+                                                       ctx->c, nullptr, ctx->s, ls->ureg, ctx->part_vol, st, SL(ctx)));
         cur ^= 1;
         LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 0, ctx->part_fwd, ctx->n_part_fwd,
-                                                                   ctx->part_vol, ctx->n_part_vol, st));
+                                                                   ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
         // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
         if (!last)
             LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
-                                                             ctx->r, ctx->rs, ctx->s, st));
+                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
         const long long ldb = lsqr_basis_stride(M);
         float *bv = (reorth && !last) ? ctx->basis + (size_t)(i - 1) * ldb : nullptr;
+        const long long bst = (long long)ctx->basis_stride;
         LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 0, last, ctx->x, ctx->g, ctx->p, ctx->s, bv, ls,
-                                                        ctx->part_vec, st));
+                                                        ctx->part_vec, st, SL(ctx), bst));
         if (last) break;
         if (reorth) {
             for (int pass = 0; pass < 2; ++pass) {
-                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ls, ctx->part_dots, st));
-                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ls, ctx->part_dots, st));
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ls, ctx->part_dots, st,
+                                                                  SL(ctx), bst));
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ls, ctx->part_dots, st, SL(ctx), bst));
                 LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_sub(M, ldb, i, ctx->basis, ctx->p, ls,
-                                                                 pass == 1 ? ctx->part_vec : nullptr, st));
+                                                                 pass == 1 ? ctx->part_vec : nullptr, st, SL(ctx),
+                                                                 bst));
             }
         }
-        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 0, ctx->part_vec, ctx->n_part_vec, st));
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 0, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
     }
     return PICCS_OK;
 }
 
+// d_b: the slots' projections, slot_bytes apart (any pointer for one slot);
+// d_x0: the slots' initial volumes, x0_pitch bytes apart.
 static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
-                               const float *d_x0)
+                               const float *d_x0, size_t x0_pitch)
 {
     cudaStream_t st = ctx->stream;
     const long long M = ctx->M, N = ctx->N;
     const float l2p = lam2_piple(p);
+    const size_t vb = M * sizeof(float), S = ctx->slot_bytes;
 
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st));
+    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st, SL(ctx)));
     if (p->x0_mode == PICCS_X0_PRIOR) {
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, ctx->xprior, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, ctx->xprior, S, vb, ctx->nslot, cudaMemcpyDeviceToDevice, st));
     } else if (p->x0_mode == PICCS_X0_ZERO) {
-        CUDA_TRY(ctx, cudaMemsetAsync(ctx->x, 0, M * sizeof(float), st));
+        CUDA_TRY(ctx, cudaMemset2DAsync(ctx->x, S, 0, vb, ctx->nslot, st));
     } else {
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->x, d_x0, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, d_x0, x0_pitch, vb, ctx->nslot, cudaMemcpyDeviceToDevice, st));
     }
     if (p->solver != PICCS_SOLVER_CGLS) {
         if (p->solver == PICCS_SOLVER_LSQR_REORTH) {
@@ -625,11 +686,11 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
             if (rc != PICCS_OK) return rc;
         }
         if (p->n_inner == 0) {  // no inner step: x stays x0; still flag NaN/Inf in b
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
             return PICCS_OK;
         }
         for (int k = 0; k < p->n_outer; ++k) {
-            int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c);
+            int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx));
             if (rc == PICCS_OK) rc = enqueue_lsqr_cycle(ctx, d_b, p, k);
             if (rc != PICCS_OK) return rc;
         }
@@ -637,38 +698,38 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
     LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,
-                                 nullptr, &ctx->ks->nonfinite, st));
+                                 nullptr, &ctx->ks->nonfinite, st, SL(ctx)));
     for (int k = 0; k < p->n_outer; ++k) {
         // reweighting at the previous iterate (Eqs. 10-11)
-        int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c);
+        int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx));
         if (rc != PICCS_OK) return rc;
         // restart: g = c - D^T Omega D x, s = A^T r + g
         if (k == 0) {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
-                                             ctx->s, 1, nullptr, st));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st));
+                                             ctx->s, 1, nullptr, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st, SL(ctx)));
         } else {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
-                                             ctx->s, 0, ctx->part_vol, st));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vol, ctx->n_part_vol, 1, st));
+                                             ctx->s, 0, ctx->part_vol, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vol, ctx->n_part_vol, 1, st, SL(ctx)));
         }
         for (int it = 0; it < p->n_inner; ++it) {
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st));
-            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p, ctx->q, FWD_PLAIN,
-                                         nullptr, ctx->part_fwd, nullptr, st));
+                                         nullptr, ctx->part_fwd, nullptr, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
-                                                ctx->part_vol, ctx->n_part_vol, st));
+                                                ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
-                                          ctx->q, ctx->ks, st));
+                                          ctx->q, ctx->ks, st, SL(ctx)));
             // after the reconstruction's last step s = A^T r + g only feeds the
             // history, so its backprojection is skipped
             if (k == p->n_outer - 1 && it == p->n_inner - 1) break;
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st));
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st, SL(ctx)));
         }
     }
     return PICCS_OK;
@@ -691,19 +752,27 @@ int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *p
 {
     int rc = check_reconstruct_args(ctx, d_proj, params, d_x0, d_vol_out);
     if (rc != PICCS_OK) return rc;
-    rc = enqueue_reconstruct(ctx, d_proj, params, d_x0);
+    const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float);
+    const float *d_b = d_proj;
+    if (ctx->nslot > 1) {  // the kernels read each slot's projections at its workspace stride
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, ctx->slot_bytes, d_proj, pb, pb, ctx->nslot,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+        d_b = ctx->bstage;
+    }
+    rc = enqueue_reconstruct(ctx, d_b, params, d_x0, vb);
     if (rc != PICCS_OK) return rc;
-    CUDA_TRY(ctx, cudaMemcpyAsync(d_vol_out, ctx->x, ctx->M * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(d_vol_out, vb, ctx->x, ctx->slot_bytes, vb, ctx->nslot,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
     return PICCS_OK;
 }
 
-int piccs_report(piccs_ctx *ctx, piccs_stats *out)
+int piccs_report_slot(piccs_ctx *ctx, int slot, piccs_stats *out)
 {
     if (!ctx || !out) return set_err(ctx, PICCS_EINVAL, "NULL argument");
+    if (slot < 0 || slot >= ctx->nslot) return set_err(ctx, PICCS_EINVAL, "slot %d out of range", slot);
     KrylovScalars ks;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    CUDA_TRY(ctx, cudaMemcpy(&ks, ctx->ks, sizeof ks, cudaMemcpyDeviceToHost));
+    CUDA_TRY(ctx, cudaMemcpy(&ks, slot_at(ctx->ks, ctx, slot), sizeof ks, cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof *out);
     out->status = ks.nonfinite ? PICCS_ENONFINITE : ks.status;
     out->iterations_run = ks.iters_run;
@@ -712,28 +781,36 @@ int piccs_report(piccs_ctx *ctx, piccs_stats *out)
     return PICCS_OK;
 }
 
+int piccs_report(piccs_ctx *ctx, piccs_stats *out)
+{
+    return piccs_report_slot(ctx, 0, out);
+}
+
 int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_params *params,
                            const float *h_x0, float *h_vol_out)
 {
     int rc = check_reconstruct_args(ctx, h_proj, params, h_x0, h_vol_out);
     if (rc != PICCS_OK) return rc;
     cudaStream_t st = ctx->stream;
-    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->bstage, h_proj, ctx->N * sizeof(float), cudaMemcpyHostToDevice, st));
+    const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float), S = ctx->slot_bytes;
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, S, h_proj, pb, pb, ctx->nslot, cudaMemcpyHostToDevice, st));
     const float *dx0 = nullptr;
     if (params->x0_mode == PICCS_X0_USER) {
-        // the initial guess goes through the p buffer, which is free until the first step
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->p, h_x0, ctx->M * sizeof(float), cudaMemcpyHostToDevice, st));
+        // the initial guesses go through the p buffers, which are free until the first step
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->p, S, h_x0, vb, vb, ctx->nslot, cudaMemcpyHostToDevice, st));
         dx0 = ctx->p;
     }
-    rc = enqueue_reconstruct(ctx, ctx->bstage, params, dx0);
+    rc = enqueue_reconstruct(ctx, ctx->bstage, params, dx0, S);
     if (rc != PICCS_OK) return rc;
-    CUDA_TRY(ctx, cudaMemcpyAsync(h_vol_out, ctx->x, ctx->M * sizeof(float), cudaMemcpyDeviceToHost, st));
-    piccs_stats rep;
-    rc = piccs_report(ctx, &rep);
-    if (rc != PICCS_OK) return rc;
-    if (rep.status != PICCS_OK)
-        return set_err(ctx, rep.status, rep.status == PICCS_ENONFINITE ? "projections hold NaN or Inf"
-                                                                       : "Krylov breakdown");
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(h_vol_out, vb, ctx->x, S, vb, ctx->nslot, cudaMemcpyDeviceToHost, st));
+    for (int sl = 0; sl < ctx->nslot; ++sl) {
+        piccs_stats rep;
+        rc = piccs_report_slot(ctx, sl, &rep);
+        if (rc != PICCS_OK) return rc;
+        if (rep.status != PICCS_OK)
+            return set_err(ctx, rep.status, rep.status == PICCS_ENONFINITE ? "projections %d hold NaN or Inf"
+                                                                           : "Krylov breakdown in scan %d", sl);
+    }
     return PICCS_OK;
 }
 

@@ -97,3 +97,18 @@ def test_solver_parameter(pk):
         with pytest.raises(pk.PiccsError) as e:
             pk.piccs_validate(g, pk.make_params(**bad))
         assert e.value.code == pk.PICCS_EINVAL
+
+
+def test_batched_workspace(pk):
+    g = P.c1_small().geometry
+    one = pk.piccs_query_workspace(g)
+    four = pk.piccs_query_workspace_batched(g, None, 4)
+    # the ray tables are shared; each further scan adds one slot
+    slot = (four - one) // 3
+    assert four == one + 3 * slot
+    assert 4 * (9 * g.M + 5 * g.N) <= slot <= 4 * (9 * g.M + 5 * g.N) + (1 << 20)
+    re = pk.piccs_query_workspace_batched(g, pk.make_params(solver=2, n_inner=5), 4)
+    assert re - four >= 4 * 4 * 4 * g.M
+    for bad in (0, -1, 65):
+        with pytest.raises(pk.PiccsError):
+            pk.piccs_query_workspace_batched(g, None, bad)
