@@ -47,14 +47,20 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solver", choices=list(SOLVERS), default="cgls",
                     help="inner Krylov solver (LSQR and CGLS are equivalent in exact arithmetic)")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="c2_needle",
+                    help="c2_needle: the 256^3 scan the headline is quoted on; c1_small: 64^3")
+    ap.add_argument("--batch", type=int, default=1,
+                    help="scans reconstructed together per step (one launch per kernel for all)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run only the projector pair on the workload (for profiler captures)")
     return ap.parse_args()
 
 
-def workload():
-    scan = P.c2_needle()
-    return scan
+WORKLOADS = {"c2_needle": P.c2_needle, "c1_small": P.c1_small}
+
+
+def workload(name="c2_needle"):
+    return WORKLOADS[name]()
 
 
 def workload_config(scan, solver="cgls", workspace_bytes=None):
@@ -62,7 +68,8 @@ def workload_config(scan, solver="cgls", workspace_bytes=None):
     ws = (f"workspace {workspace_bytes / 1e9:.2f} GB" if workspace_bytes
           else "working set larger than L2")
     return {
-        "workload": (f"{scan.name}: {g.nx}^3 x {g.vx:g} mm volume, {g.n_views} views over 200 deg, "
+        "workload": (f"{scan.name}: {g.nx}^3 x {g.vx:g} mm volume, {g.n_views} views over "
+                     f"{np.degrees((g.angles[1] - g.angles[0]) * g.n_views):.0f} deg, "
                      f"{g.nu}x{g.nv} detector x {g.du:g} mm, DSO {g.dso:g} / DSD {g.dsd:g} mm, "
                      f"IRN-PICCS {scan.n_outer} cycles x {scan.n_inner} "
                      f"{SOLVERS[solver][1]} iterations"),
@@ -243,7 +250,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    scan = workload()
+    scan = workload(args.workload)
     b = scan.measured()
     xp = scan.prior_volume(ss=1)
     for _ in range(args.warmup):
@@ -283,7 +290,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2509_08574_gb300 as pk
 
-    scan = workload()
+    scan = workload(args.workload)
     g = scan.geometry
     t_in = time.perf_counter()
     b_np = scan.measured()
@@ -291,14 +298,18 @@ def run_ours(args):
     t_in = time.perf_counter() - t_in
 
     stream = torch.cuda.Stream()
+    B = max(1, args.batch)
     b = torch.from_numpy(b_np).cuda()
     xp = torch.from_numpy(xp_np).cuda()
-    out = torch.empty(g.vol_shape(), dtype=torch.float32, device="cuda")
+    if B > 1:  # B scans of the workload, reconstructed together
+        b = b.unsqueeze(0).expand((B,) + tuple(b.shape)).contiguous()
+        xp = xp.unsqueeze(0).expand((B,) + tuple(xp.shape)).contiguous()
+    out = torch.empty(((B,) if B > 1 else ()) + g.vol_shape(), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner,
                             solver=SOLVERS[args.solver][0])
     torch.cuda.synchronize()
-    ctx = pk.Context(g, stream=stream)
+    ctx = pk.Context(g, stream=stream, batch=B)
     ctx.set_prior(xp)
 
     with torch.cuda.stream(stream):
@@ -306,9 +317,11 @@ def run_ours(args):
             flush.zero_()
             ctx.reconstruct(b, params, out=out)
     stream.synchronize()
-    rep = ctx.report()
-    if rep.status != 0 or rep.iterations_run != scan.iterations:
-        raise RuntimeError(f"reconstruction status {rep.status}, {rep.iterations_run} iterations")
+    for slot in range(B):
+        rep = ctx.report(slot)
+        if rep.status != 0 or rep.iterations_run != scan.iterations:
+            raise RuntimeError(f"reconstruction {slot}: status {rep.status}, "
+                               f"{rep.iterations_run} iterations")
 
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -331,15 +344,15 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     prof = ctx.profile_read()
-    step_ms = [a.elapsed_time(c) for a, c in ev]
+    step_ms = [a.elapsed_time(c) / B for a, c in ev]  # per scan
     p50, p99 = pctl(step_ms, 50), pctl(step_ms, 99)
     total_ms = float(sum(step_ms))
 
     p50, p99, total_ms = max_over_ranks([p50, p99, total_ms], "cuda")
 
     # end to end through the public API with host buffers (copies inside)
-    hb = torch.from_numpy(b_np).pin_memory()
-    hout = torch.empty(g.vol_shape(), dtype=torch.float32).pin_memory()
+    hb = b.cpu().pin_memory()
+    hout = torch.empty(tuple(out.shape), dtype=torch.float32).pin_memory()
     ctx.set_stream(stream)
     e2e_ms = []
     for k in range(args.e2e_steps + 1):
@@ -348,7 +361,7 @@ def run_ours(args):
         stream.synchronize()
         t0 = time.perf_counter()
         ctx.reconstruct_host(hb, params, out=hout)
-        dt = (time.perf_counter() - t0) * 1e3
+        dt = (time.perf_counter() - t0) * 1e3 / B
         if k > 0:  # first call warms the pinned-memory path
             e2e_ms.append(dt)
     e2e_p50 = max_over_ranks([pctl(e2e_ms, 50)], "cuda")[0]
@@ -357,9 +370,9 @@ def run_ours(args):
     nnz = nnz_of(scan)
     peaks, peak_kind = measured_peaks()
     per = {}
-    for kind in ("forward", "adjoint"):
+    for kind in ("forward", "adjoint"):  # per scan: a batched launch serves B scans
         n = prof["launches"][kind]
-        per[kind] = (prof["total_ms"][kind] / n) if n else float("nan")
+        per[kind] = (prof["total_ms"][kind] / n / B) if n else float("nan")
     dom = max(("forward", "adjoint"), key=lambda k: prof["total_ms"][k])
     alg_bytes = 4.0 * (nnz + g.M + g.N)
     achieved = alg_bytes / (per[dom] * 1e-3) / 1e9
@@ -368,15 +381,18 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "warmup": args.warmup, "ms_per_step": total_ms * B / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(scan, args.solver, pk.piccs_query_workspace(g, params)),
+        "config": dict(workload_config(scan, args.solver,
+                                       pk.piccs_query_workspace_batched(g, params, B)),
+                       batch=B),
         "p50_ms": p50, "p99_ms": p99,
-        "job_scans_per_s": world * args.steps / (total_ms * 1e-3),
-        "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(g.N * 4),
-                "d2h_bytes_per_step": int(g.M * 4)},
+        "job_scans_per_s": world * args.steps * B / (total_ms * B * 1e-3),
+        "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(B * g.N * 4),
+                "d2h_bytes_per_step": int(B * g.M * 4)},
         "gpu_launches": int(prof["total_launches"]),
         "kernel_ms_per_step": {k: v / args.steps for k, v in prof["total_ms"].items()},
+        "kernel_ms_per_scan": {k: v / args.steps / B for k, v in prof["total_ms"].items()},
         "launches_per_step": {k: v / args.steps for k, v in prof["launches"].items()},
         "projector": {"nnz": nnz, "fwd_ms": per["forward"], "adj_ms": per["adjoint"],
                       "fwd_gups": nnz / (per["forward"] * 1e-3) / 1e9,
@@ -406,7 +422,7 @@ def run_kernels_only(args):
     import torch
     import paper_2509_08574_gb300 as pk
 
-    scan = workload()
+    scan = workload(args.workload)
     g = scan.geometry
     x = torch.from_numpy(scan.prior_volume(ss=1)).cuda()
     y = torch.from_numpy(P.random_projections(g, 7).astype(np.float32)).cuda()
