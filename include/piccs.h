@@ -204,6 +204,23 @@ int piccs_report(piccs_ctx *ctx, piccs_stats *out);
 /* The same for slot `slot` (0 <= slot < batch) of a batched context. */
 int piccs_report_slot(piccs_ctx *ctx, int slot, piccs_stats *out);
 
+/* Staged reconstructions: the building blocks of a request loop that keeps a
+ * context per patient resident and feeds it scans as they arrive.
+ * piccs_set_prior_broadcast copies one prior volume (host or device, M
+ * floats) into every slot and checks it (synchronises).  piccs_stage copies
+ * one scan's projections (N floats, host or device) into slot `slot`'s
+ * staging buffer; piccs_run_staged reconstructs slots 0 .. nactive-1 from
+ * their staged projections (x0_mode PRIOR or ZERO); piccs_unstage copies slot
+ * `slot`'s volume out.  All three are asynchronous on the context's stream
+ * (host buffers should be pinned).  use_graph != 0: the launch sequence of a
+ * (params, nactive) pair is captured once as a CUDA graph and replayed (the
+ * per-step scalars stay on the device, so a replay is a full reconstruction);
+ * the first run of each pair synchronises for the capture. */
+int piccs_set_prior_broadcast(piccs_ctx *ctx, const float *xprior, int from_host);
+int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host);
+int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph);
+int piccs_unstage(piccs_ctx *ctx, int slot, float *vol, int to_host);
+
 /* Forward projection d_proj = A d_vol (Eq. 1): N floats from M floats (each
  * of the batch's volumes in a batched context, one launch per volume). */
 int piccs_forward(piccs_ctx *ctx, const float *d_vol, float *d_proj);

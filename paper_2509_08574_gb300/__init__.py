@@ -63,6 +63,23 @@ class piccs_stats(C.Structure):
                 ("gamma_history", C.c_double * 512)]
 
 
+class piccs_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("max_running", C.c_int),
+                ("use_graphs", C.c_int)]
+
+
+class piccs_request_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("batch", C.c_int), ("queued_ms", C.c_double),
+                ("run_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class piccs_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("batches", C.c_longlong), ("graph_replays", C.c_longlong),
+                ("sessions_made", C.c_longlong), ("evictions", C.c_longlong),
+                ("hbm_in_use", C.c_size_t)]
+
+
 KERNEL_CLASSES = ("forward", "adjoint", "reg", "vector", "scalar")
 
 
@@ -83,6 +100,17 @@ def _load():
         "piccs_create_batched": (i, [C.POINTER(vp), G, i, vp]),
         "piccs_query_workspace_batched": (i, [G, P, i, C.POINTER(C.c_size_t)]),
         "piccs_report_slot": (i, [vp, i, R]),
+        "piccs_set_prior_broadcast": (i, [vp, vp, i]),
+        "piccs_stage": (i, [vp, i, vp, i]),
+        "piccs_run_staged": (i, [vp, i, P, i]),
+        "piccs_unstage": (i, [vp, i, vp, i]),
+        "piccs_server_create": (i, [C.POINTER(vp), C.POINTER(piccs_server_config)]),
+        "piccs_server_destroy": (None, [vp]),
+        "piccs_server_last_error": (C.c_char_p, [vp]),
+        "piccs_server_add_patient": (i, [vp, i, G, vp]),
+        "piccs_server_submit": (i, [vp, i, vp, P, vp, C.POINTER(C.c_longlong)]),
+        "piccs_server_wait": (i, [vp, C.c_longlong, i, C.POINTER(piccs_request_stats)]),
+        "piccs_server_get_stats": (i, [vp, C.POINTER(piccs_server_stats)]),
         "piccs_destroy": (None, [vp]),
         "piccs_last_error": (C.c_char_p, [vp]),
         "piccs_set_stream": (i, [vp, vp]),
@@ -113,7 +141,10 @@ EXPORTED = ("piccs_create", "piccs_destroy", "piccs_last_error", "piccs_set_stre
             "piccs_reconstruct_host", "piccs_report", "piccs_forward", "piccs_adjoint",
             "piccs_reg_weights", "piccs_reg_normal", "piccs_profile_enable",
             "piccs_profile_read", "piccs_reg_normal_noalloc", "piccs_create_batched",
-            "piccs_query_workspace_batched", "piccs_report_slot")
+            "piccs_query_workspace_batched", "piccs_report_slot", "piccs_set_prior_broadcast",
+            "piccs_stage", "piccs_run_staged", "piccs_unstage", "piccs_server_create",
+            "piccs_server_destroy", "piccs_server_last_error", "piccs_server_add_patient",
+            "piccs_server_submit", "piccs_server_wait", "piccs_server_get_stats")
 
 
 def library():
@@ -415,3 +446,81 @@ class Context:
         out = torch.empty_like(z) if out is None else out
         rho = piccs_reg_normal(self.h, omega, params, z, out, True)
         return out, rho
+
+
+# --------------------------------------------------------------------------
+# request server (include/piccs_server.h)
+# --------------------------------------------------------------------------
+def _check_srv(rc, srv):
+    if rc != PICCS_OK:
+        m = _lib.piccs_server_last_error(srv)
+        raise PiccsError(rc, (m.decode() if m else "") or _NAMES.get(rc, str(rc)))
+
+
+class Server:
+    """A request loop for repeated scans: per-patient device sessions admitted
+    by HBM footprint, continuous batching, overlapped batches, CUDA graphs.
+    Buffers handed to submit() are kept referenced until wait() returns."""
+
+    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True):
+        cfg = piccs_server_config(int(hbm_budget), int(max_batch), int(max_running),
+                                  1 if use_graphs else 0)
+        h = C.c_void_p()
+        _check_srv(_lib.piccs_server_create(C.byref(h), C.byref(cfg)), None)
+        self.h = h.value
+        self._held = {}
+        self._shapes = {}
+
+    def close(self):
+        if self.h:
+            _lib.piccs_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_patient(self, patient, geometry, prior):
+        gs = geometry if isinstance(geometry, piccs_geometry) else make_geometry(geometry)
+        M = gs.nx * gs.ny * gs.nz
+        prior = np.ascontiguousarray(prior, dtype=np.float32)
+        _check_srv(_lib.piccs_server_add_patient(self.h, int(patient), C.byref(gs),
+                                                 _ptr(prior, M, "prior")), self.h)
+        self._shapes[int(patient)] = (gs.n_views * gs.nu * gs.nv, (gs.nx, gs.ny, gs.nz))
+
+    def submit(self, patient, proj, params, out=None):
+        """proj: host projections (pinned torch tensor or numpy array); returns
+        (ticket, out)."""
+        N, vol_shape = self._shapes[int(patient)]
+        if out is None:
+            out = np.empty(vol_shape, dtype=np.float32)
+        t = C.c_longlong(0)
+        _check_srv(_lib.piccs_server_submit(self.h, int(patient), _ptr(proj, N, "projections"),
+                                            C.byref(params), _ptr(out, int(np.prod(vol_shape)),
+                                                                  "volume"), C.byref(t)), self.h)
+        self._held[t.value] = (proj, out, params)
+        return t.value, out
+
+    def wait(self, ticket, timeout_ms=-1) -> dict:
+        st = piccs_request_stats()
+        rc = _lib.piccs_server_wait(self.h, int(ticket), int(timeout_ms), C.byref(st))
+        if rc == PICCS_ETIMEOUT:
+            return None
+        _check_srv(rc, self.h)
+        self._held.pop(int(ticket), None)
+        return {"status": st.status, "batch": st.batch, "queued_ms": st.queued_ms,
+                "run_ms": st.run_ms, "total_ms": st.total_ms}
+
+    def stats(self) -> dict:
+        st = piccs_server_stats()
+        _check_srv(_lib.piccs_server_get_stats(self.h, C.byref(st)), self.h)
+        return {k: int(getattr(st, k)) for k, _ in piccs_server_stats._fields_}

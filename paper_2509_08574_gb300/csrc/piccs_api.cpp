@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,7 @@ struct piccs_ctx {
     VolDims vd;
     long long M = 0, N = 0;
     int nslot = 1;              // scans per batch (same geometry)
+    int nactive = 1;            // slots the current call works on (a prefix)
     size_t slot_bytes = 0;      // stride between the slots' workspaces
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -58,6 +60,10 @@ struct piccs_ctx {
     int *flag = nullptr;
     double *dsum = nullptr;
 
+    // CUDA graphs of staged reconstructions, by (params, active slots)
+    struct GraphEntry { cudaGraphExec_t exec = nullptr; long long launches[PICCS_KERNEL_CLASSES] = {}; };
+    std::map<std::string, GraphEntry> graphs;
+    long long graph_launches = 0;
     // kernel accounting
     bool timing = false;
     long long launches[PICCS_KERNEL_CLASSES] = {};
@@ -133,7 +139,7 @@ struct Launch {
 };
 
 // all slots of the context in one launch
-#define SL(ctx) Slots{(ctx)->nslot, (long long)(ctx)->slot_bytes}
+#define SL(ctx) Slots{(ctx)->nactive, (long long)(ctx)->slot_bytes}
 
 #define LAUNCH(ctx, kind, call)                          \
     do {                                                 \
@@ -358,6 +364,7 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
     ctx->hit_ptr = reinterpret_cast<int *>(b + L.off_hitptr);
     ctx->hits = reinterpret_cast<CellHit *>(b + L.off_hits);
     ctx->nslot = batch;
+    ctx->nactive = batch;
     ctx->slot_bytes = L.slot_bytes;
     b += L.off_slot0;  // slot 0; slot s is s * slot_bytes further
     float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
@@ -416,6 +423,7 @@ void piccs_destroy(piccs_ctx *ctx)
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.exec);
     cudaFree(ctx->basis);
     cudaFree(ctx->base);
     delete ctx;
@@ -469,7 +477,7 @@ int piccs_set_prior(piccs_ctx *ctx, const float *d_xprior)
 {
     if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
     if (!d_xprior) return set_err(ctx, PICCS_EINVAL, "d_xprior is NULL");
-    const int B = ctx->nslot;
+    const int B = ctx->nactive = ctx->nslot;
     const size_t vb = ctx->M * sizeof(float);
     CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->xprior, ctx->slot_bytes, d_xprior, vb, vb, B,
                                     cudaMemcpyDeviceToDevice, ctx->stream));
@@ -674,11 +682,11 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
 
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st, SL(ctx)));
     if (p->x0_mode == PICCS_X0_PRIOR) {
-        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, ctx->xprior, S, vb, ctx->nslot, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, ctx->xprior, S, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
     } else if (p->x0_mode == PICCS_X0_ZERO) {
-        CUDA_TRY(ctx, cudaMemset2DAsync(ctx->x, S, 0, vb, ctx->nslot, st));
+        CUDA_TRY(ctx, cudaMemset2DAsync(ctx->x, S, 0, vb, ctx->nactive, st));
     } else {
-        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, d_x0, x0_pitch, vb, ctx->nslot, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, d_x0, x0_pitch, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
     }
     if (p->solver != PICCS_SOLVER_CGLS) {
         if (p->solver == PICCS_SOLVER_LSQR_REORTH) {
@@ -752,6 +760,7 @@ int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *p
 {
     int rc = check_reconstruct_args(ctx, d_proj, params, d_x0, d_vol_out);
     if (rc != PICCS_OK) return rc;
+    ctx->nactive = ctx->nslot;
     const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float);
     const float *d_b = d_proj;
     if (ctx->nslot > 1) {  // the kernels read each slot's projections at its workspace stride
@@ -791,6 +800,7 @@ int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_para
 {
     int rc = check_reconstruct_args(ctx, h_proj, params, h_x0, h_vol_out);
     if (rc != PICCS_OK) return rc;
+    ctx->nactive = ctx->nslot;
     cudaStream_t st = ctx->stream;
     const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float), S = ctx->slot_bytes;
     CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, S, h_proj, pb, pb, ctx->nslot, cudaMemcpyHostToDevice, st));
@@ -811,6 +821,94 @@ int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_para
             return set_err(ctx, rep.status, rep.status == PICCS_ENONFINITE ? "projections %d hold NaN or Inf"
                                                                            : "Krylov breakdown in scan %d", sl);
     }
+    return PICCS_OK;
+}
+
+// ---- staged reconstructions (the building blocks of the request server) ----
+
+int piccs_set_prior_broadcast(piccs_ctx *ctx, const float *xprior, int from_host)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (!xprior) return set_err(ctx, PICCS_EINVAL, "xprior is NULL");
+    const size_t vb = ctx->M * sizeof(float);
+    for (int b = 0; b < ctx->nslot; ++b)
+        CUDA_TRY(ctx, cudaMemcpyAsync(slot_at(ctx->xprior, ctx, b), b == 0 ? xprior : ctx->xprior, vb,
+                                      b == 0 && from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    ctx->nactive = 1;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(ctx->M, ctx->xprior, ctx->flag, ctx->stream));
+    int bad = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&bad, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->has_prior = !bad;
+    if (bad) return set_err(ctx, PICCS_ENONFINITE, "prior volume holds NaN or Inf");
+    return PICCS_OK;
+}
+
+int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (slot < 0 || slot >= ctx->nslot || !proj) return set_err(ctx, PICCS_EINVAL, "bad slot or NULL buffer");
+    CUDA_TRY(ctx, cudaMemcpyAsync(slot_at(ctx->bstage, ctx, slot), proj, ctx->N * sizeof(float),
+                                  from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    return PICCS_OK;
+}
+
+int piccs_unstage(piccs_ctx *ctx, int slot, float *vol, int to_host)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (slot < 0 || slot >= ctx->nslot || !vol) return set_err(ctx, PICCS_EINVAL, "bad slot or NULL buffer");
+    CUDA_TRY(ctx, cudaMemcpyAsync(vol, slot_at(ctx->x, ctx, slot), ctx->M * sizeof(float),
+                                  to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    return PICCS_OK;
+}
+
+int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    char why[256];
+    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(ctx, PICCS_EINVAL, "%s", why);
+    if (nactive < 1 || nactive > ctx->nslot) return set_err(ctx, PICCS_EINVAL, "nactive %d out of range", nactive);
+    if (params->x0_mode == PICCS_X0_USER) return set_err(ctx, PICCS_EINVAL, "staged runs start from the prior or zero");
+    if (needs_prior(params) && !ctx->has_prior) return set_err(ctx, PICCS_EINVAL, "prior not set");
+    ctx->nactive = nactive;
+    if (params->solver == PICCS_SOLVER_LSQR_REORTH) {  // allocate before any capture
+        int rc = ensure_basis(ctx, params->n_inner);
+        if (rc != PICCS_OK) return rc;
+    }
+    if (!use_graph || ctx->timing) return enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);
+    // one CUDA graph per (parameters, active slots): the launch sequence is
+    // fixed, every per-step scalar lives on the device
+    std::string key(reinterpret_cast<const char *>(params), sizeof *params);
+    key.append(reinterpret_cast<const char *>(&nactive), sizeof nactive);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        long long before[PICCS_KERNEL_CLASSES];
+        std::memcpy(before, ctx->launches, sizeof before);
+        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (rc != PICCS_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != PICCS_OK ? rc : set_err(ctx, PICCS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return set_err(ctx, PICCS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        piccs_ctx::GraphEntry ge;
+        ge.exec = exec;
+        for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
+            ge.launches[k] = ctx->launches[k] - before[k];
+            ctx->launches[k] = before[k];  // counted when the graph runs
+        }
+        it = ctx->graphs.emplace(key, ge).first;
+    }
+    CUDA_TRY(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
+    for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) ctx->launches[k] += it->second.launches[k];
+    ctx->graph_launches += 1;
     return PICCS_OK;
 }
 

@@ -1,0 +1,506 @@
+// Request loop for repeated scans (include/piccs_server.h): per-patient
+// device sessions admitted by HBM footprint, continuous batching of a
+// patient's queued scans into one batched reconstruction, several batches in
+// flight on their own streams, CUDA-graph replay of each launch sequence.
+//
+// Threads: callers only touch the queues under `mu`; one worker thread owns
+// every session and issues all CUDA work.  A batch's completion is signalled
+// by a host function enqueued behind its last copy, which wakes the worker.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/piccs_server.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+    long long id = 0;
+    int patient = 0;
+    const float *h_proj = nullptr;
+    float *h_out = nullptr;
+    piccs_params params{};
+    Clock::time_point t_submit, t_issue, t_done;
+    int status = PICCS_OK;
+    int batch = 0;
+    bool done = false;
+};
+
+struct Session {
+    int patient = 0;
+    piccs_geometry geo{};
+    std::vector<double> angles;
+    std::vector<float> prior;
+    size_t bytes = 0;  // device bytes held while resident
+    piccs_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::deque<Request *> queue;
+    std::vector<Request *> running;
+    bool finished = false;  // set by the completion host function (under mu)
+    long long last_used = 0;
+};
+
+struct PendingPatient {
+    int patient;
+    piccs_geometry geo;
+    std::vector<double> angles;
+    std::vector<float> prior;
+};
+
+thread_local std::string g_create_err;
+
+}  // namespace
+
+struct piccs_server {
+    piccs_server_config cfg{};
+    int device = 0;
+    std::string err;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::set<int> registered;                 // under mu
+    std::deque<PendingPatient> new_patients;  // under mu
+    std::deque<Request *> incoming;           // under mu
+    std::map<long long, Request *> requests;  // under mu
+    bool stop = false;                        // under mu
+    bool wake = false;                        // under mu
+    long long next_id = 1;                    // under mu
+    piccs_server_stats st{};                  // under mu
+    std::map<int, Session> sessions;          // worker only
+    long long tick = 0;                       // worker only
+    std::thread worker;
+};
+
+namespace {
+
+int fail(piccs_server *srv, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (srv) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->err = buf;
+    } else {
+        g_create_err = buf;
+    }
+    return code;
+}
+
+struct DoneArg {
+    piccs_server *srv;
+    Session *ses;
+};
+
+// Runs on a CUDA driver thread once a batch's last copy has finished: no
+// CUDA calls here, only the wake-up.
+void CUDART_CB batch_done(void *p)
+{
+    DoneArg *a = static_cast<DoneArg *>(p);
+    {
+        std::lock_guard<std::mutex> lk(a->srv->mu);
+        a->ses->finished = true;
+        a->srv->wake = true;
+    }
+    a->srv->cv_work.notify_one();
+    delete a;
+}
+
+void finish_requests(piccs_server *srv, std::vector<Request *> &reqs, int status_if_unset)
+{
+    const auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (Request *r : reqs) {
+            if (r->status == PICCS_OK && status_if_unset != PICCS_OK) r->status = status_if_unset;
+            r->t_done = now;
+            r->done = true;
+            if (r->status == PICCS_OK) srv->st.completed += 1;
+            else srv->st.failed += 1;
+        }
+    }
+    reqs.clear();
+    srv->cv_done.notify_all();
+}
+
+void evict(piccs_server *srv, Session &s)
+{
+    if (!s.ctx) return;
+    piccs_destroy(s.ctx);
+    cudaStreamDestroy(s.stream);
+    s.ctx = nullptr;
+    s.stream = nullptr;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->st.hbm_in_use -= s.bytes;
+    s.bytes = 0;
+}
+
+// Makes the session resident with room for `params` (creating it, evicting
+// idle sessions if the budget requires).  Returns PICCS_OK, 1 if it has to
+// wait for memory to free up, or an error.
+int make_resident(piccs_server *srv, Session &s, const piccs_params &params)
+{
+    size_t need = 0;
+    int rc = piccs_query_workspace_batched(&s.geo, &params, srv->cfg.max_batch, &need);
+    if (rc != PICCS_OK) return rc;
+    if (s.ctx && need <= s.bytes) return PICCS_OK;
+    size_t used;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        used = srv->st.hbm_in_use;
+    }
+    const size_t extra = need - s.bytes;
+    while (used + extra > srv->cfg.hbm_budget) {
+        Session *lru = nullptr;
+        for (auto &kv : srv->sessions) {
+            Session &o = kv.second;
+            if (&o == &s || !o.ctx || !o.running.empty() || !o.queue.empty()) continue;
+            if (!lru || o.last_used < lru->last_used) lru = &o;
+        }
+        if (!lru) return 1;
+        const size_t freed = lru->bytes;
+        evict(srv, *lru);
+        used -= freed;
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->st.evictions += 1;
+    }
+    if (!s.ctx) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return PICCS_ECUDA;
+        }
+        rc = piccs_create_batched(&s.ctx, &s.geo, srv->cfg.max_batch, s.stream);
+        if (rc == PICCS_OK) rc = piccs_set_prior_broadcast(s.ctx, s.prior.data(), 1);
+        if (rc != PICCS_OK) {
+            if (s.ctx) piccs_destroy(s.ctx);
+            cudaStreamDestroy(s.stream);
+            s.ctx = nullptr;
+            s.stream = nullptr;
+            return rc;
+        }
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->st.sessions_made += 1;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->st.hbm_in_use += extra;
+    s.bytes = need;
+    return PICCS_OK;
+}
+
+bool same_params(const piccs_params &a, const piccs_params &b)
+{
+    return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+// Issues the next batch of session s; false if it has to wait for memory.
+bool issue_batch(piccs_server *srv, Session &s)
+{
+    Request *head = s.queue.front();
+    int rc = make_resident(srv, s, head->params);
+    if (rc == 1) return false;
+    std::vector<Request *> batch;
+    if (rc != PICCS_OK) {  // this request cannot run: fail it alone
+        s.queue.pop_front();
+        head->status = rc;
+        batch.push_back(head);
+        finish_requests(srv, batch, rc);
+        return true;
+    }
+    for (auto it = s.queue.begin(); it != s.queue.end() && (int)batch.size() < srv->cfg.max_batch;) {
+        if (same_params((*it)->params, head->params)) {
+            batch.push_back(*it);
+            it = s.queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    const int n = (int)batch.size();
+    const auto now = Clock::now();
+    for (int i = 0; i < n; ++i) {
+        batch[i]->t_issue = now;
+        batch[i]->batch = n;
+        if (rc == PICCS_OK) rc = piccs_stage(s.ctx, i, batch[i]->h_proj, 1);
+    }
+    if (rc == PICCS_OK) rc = piccs_run_staged(s.ctx, n, &head->params, srv->cfg.use_graphs);
+    for (int i = 0; i < n && rc == PICCS_OK; ++i) rc = piccs_unstage(s.ctx, i, batch[i]->h_out, 1);
+    if (rc == PICCS_OK) {
+        DoneArg *a = new (std::nothrow) DoneArg{srv, &s};
+        if (!a || cudaLaunchHostFunc(s.stream, batch_done, a) != cudaSuccess) {
+            delete a;
+            cudaGetLastError();
+            rc = PICCS_ECUDA;
+        }
+    }
+    if (rc != PICCS_OK) {  // the session's state is unknown: drop it, it is re-created on demand
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        evict(srv, s);
+        finish_requests(srv, batch, rc);
+        return true;
+    }
+    s.running = std::move(batch);
+    s.last_used = ++srv->tick;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->st.batches += 1;
+    if (srv->cfg.use_graphs) srv->st.graph_replays += 1;
+    return true;
+}
+
+void collect(piccs_server *srv, Session &s)
+{
+    for (int i = 0; i < (int)s.running.size(); ++i) {
+        piccs_stats rep;
+        int rc = piccs_report_slot(s.ctx, i, &rep);
+        s.running[i]->status = rc != PICCS_OK ? rc : rep.status;
+    }
+    finish_requests(srv, s.running, PICCS_OK);
+}
+
+void worker_main(piccs_server *srv)
+{
+    cudaSetDevice(srv->device);
+    bool in_flight = false;
+    for (;;) {
+        std::deque<Request *> arrived;
+        std::deque<PendingPatient> patients;
+        std::vector<Session *> finished;
+        bool stopping;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            // a stopping server still waits for the completions of its batches
+            srv->cv_work.wait(lk, [&] { return srv->wake || (srv->stop && !in_flight); });
+            srv->wake = false;
+            arrived.swap(srv->incoming);
+            patients.swap(srv->new_patients);
+            for (auto &kv : srv->sessions)
+                if (kv.second.finished) {
+                    kv.second.finished = false;
+                    finished.push_back(&kv.second);
+                }
+            stopping = srv->stop;
+        }
+        for (auto &pp : patients) {
+            Session &s = srv->sessions[pp.patient];
+            s.patient = pp.patient;
+            s.angles = std::move(pp.angles);
+            s.geo = pp.geo;
+            s.geo.angles_rad = s.angles.data();
+            s.prior = std::move(pp.prior);
+        }
+        for (Request *r : arrived) srv->sessions[r->patient].queue.push_back(r);
+        for (Session *s : finished) collect(srv, *s);
+
+        // issue: sessions whose oldest request waits longest go first
+        int running = 0;
+        for (auto &kv : srv->sessions) running += !kv.second.running.empty();
+        bool progress = true;
+        while (progress && running < srv->cfg.max_running) {
+            progress = false;
+            Session *best = nullptr;
+            for (auto &kv : srv->sessions) {
+                Session &s = kv.second;
+                if (!s.running.empty() || s.queue.empty()) continue;
+                if (!best || s.queue.front()->id < best->queue.front()->id) best = &s;
+            }
+            if (!best) break;
+            if (issue_batch(srv, *best)) {
+                progress = true;
+                running += !best->running.empty();
+            } else {
+                // wait for memory: try sessions that are already resident
+                for (auto &kv : srv->sessions) {
+                    Session &s = kv.second;
+                    if (&s == best || !s.running.empty() || s.queue.empty() || !s.ctx) continue;
+                    if (issue_batch(srv, s)) {
+                        progress = true;
+                        running += !s.running.empty();
+                        break;
+                    }
+                }
+            }
+        }
+        bool idle = true;
+        for (auto &kv : srv->sessions)
+            if (!kv.second.running.empty() || !kv.second.queue.empty()) idle = false;
+        in_flight = running > 0;
+        if (stopping && idle) {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            if (srv->incoming.empty() && srv->new_patients.empty()) break;
+        }
+        if (!idle && running == 0) {
+            // queued work that cannot be admitted and nothing running to free memory
+            for (auto &kv : srv->sessions) {
+                Session &s = kv.second;
+                std::vector<Request *> stuck(s.queue.begin(), s.queue.end());
+                s.queue.clear();
+                finish_requests(srv, stuck, PICCS_ENOMEM);
+            }
+        }
+    }
+    for (auto &kv : srv->sessions) evict(srv, kv.second);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *piccs_server_last_error(const piccs_server *srv)
+{
+    return srv ? srv->err.c_str() : g_create_err.c_str();
+}
+
+int piccs_server_create(piccs_server **out, const piccs_server_config *cfg)
+{
+    if (!out || !cfg) return fail(nullptr, PICCS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cfg->max_batch < 1 || cfg->max_batch > 64) return fail(nullptr, PICCS_EINVAL, "max_batch must be in [1, 64]");
+    if (cfg->max_running < 1) return fail(nullptr, PICCS_EINVAL, "max_running must be >= 1");
+    piccs_server *srv = new (std::nothrow) piccs_server();
+    if (!srv) return fail(nullptr, PICCS_ENOMEM, "host allocation failed");
+    srv->cfg = *cfg;
+    cudaGetDevice(&srv->device);
+    if (srv->cfg.hbm_budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            delete srv;
+            return fail(nullptr, PICCS_ECUDA, "cudaMemGetInfo failed");
+        }
+        srv->cfg.hbm_budget = free_b / 10 * 9;
+    }
+    srv->worker = std::thread(worker_main, srv);
+    *out = srv;
+    return PICCS_OK;
+}
+
+void piccs_server_destroy(piccs_server *srv)
+{
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_one();
+    srv->worker.join();
+    for (auto &kv : srv->requests) delete kv.second;
+    delete srv;
+}
+
+int piccs_server_add_patient(piccs_server *srv, int patient, const piccs_geometry *geometry,
+                             const float *h_xprior)
+{
+    if (!srv || !geometry || !h_xprior) return fail(srv, PICCS_EINVAL, "NULL argument");
+    int rc = piccs_validate(geometry, nullptr);
+    if (rc != PICCS_OK) return fail(srv, rc, "%s", piccs_last_error(nullptr));
+    size_t need = 0;
+    rc = piccs_query_workspace_batched(geometry, nullptr, srv->cfg.max_batch, &need);
+    if (rc != PICCS_OK) return fail(srv, rc, "%s", piccs_last_error(nullptr));
+    if (need > srv->cfg.hbm_budget)
+        return fail(srv, PICCS_ENOMEM, "session needs %zu bytes, budget %zu", need, srv->cfg.hbm_budget);
+    PendingPatient pp;
+    pp.patient = patient;
+    pp.geo = *geometry;
+    pp.angles.assign(geometry->angles_rad, geometry->angles_rad + geometry->n_views);
+    const size_t M = (size_t)geometry->nx * geometry->ny * geometry->nz;
+    pp.prior.assign(h_xprior, h_xprior + M);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (!srv->registered.insert(patient).second) {
+            srv->err = "patient already registered";
+            return PICCS_EINVAL;
+        }
+        srv->new_patients.push_back(std::move(pp));
+        srv->wake = true;
+    }
+    srv->cv_work.notify_one();
+    return PICCS_OK;
+}
+
+int piccs_server_submit(piccs_server *srv, int patient, const float *h_proj,
+                        const piccs_params *params, float *h_out, long long *ticket)
+{
+    if (!srv || !h_proj || !params || !h_out || !ticket) return fail(srv, PICCS_EINVAL, "NULL argument");
+    if (params->x0_mode == PICCS_X0_USER) return fail(srv, PICCS_EINVAL, "requests start from the prior or zero");
+    Request *r = new (std::nothrow) Request();
+    if (!r) return fail(srv, PICCS_ENOMEM, "host allocation failed");
+    r->patient = patient;
+    r->h_proj = h_proj;
+    r->h_out = h_out;
+    r->params = *params;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (!srv->registered.count(patient)) {
+            delete r;
+            srv->err = "unknown patient";
+            return PICCS_EINVAL;
+        }
+        if (srv->stop) {
+            delete r;
+            srv->err = "server is stopping";
+            return PICCS_EINVAL;
+        }
+        r->id = srv->next_id++;
+        srv->requests[r->id] = r;
+        srv->incoming.push_back(r);
+        srv->st.submitted += 1;
+        srv->wake = true;
+        *ticket = r->id;
+    }
+    srv->cv_work.notify_one();
+    return PICCS_OK;
+}
+
+int piccs_server_wait(piccs_server *srv, long long ticket, int timeout_ms, piccs_request_stats *st)
+{
+    if (!srv || !st) return fail(srv, PICCS_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->requests.find(ticket);
+    if (it == srv->requests.end()) {
+        srv->err = "unknown ticket";
+        return PICCS_EINVAL;
+    }
+    Request *r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(lk, ready);
+    } else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        return PICCS_ETIMEOUT;
+    }
+    st->status = r->status;
+    st->batch = r->batch;
+    st->queued_ms = r->batch ? ms_between(r->t_submit, r->t_issue) : ms_between(r->t_submit, r->t_done);
+    st->run_ms = r->batch ? ms_between(r->t_issue, r->t_done) : 0.0;
+    st->total_ms = ms_between(r->t_submit, r->t_done);
+    srv->requests.erase(it);
+    delete r;
+    return PICCS_OK;
+}
+
+int piccs_server_get_stats(piccs_server *srv, piccs_server_stats *out)
+{
+    if (!srv || !out) return fail(srv, PICCS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->st;
+    return PICCS_OK;
+}
+
+}  // extern "C"
