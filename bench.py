@@ -51,6 +51,11 @@ def parse_args():
                     help="c2_needle: the 256^3 scan the headline is quoted on; c1_small: 64^3")
     ap.add_argument("--batch", type=int, default=1,
                     help="scans reconstructed together per step (one launch per kernel for all)")
+    ap.add_argument("--serving", action="store_true",
+                    help="request-stream benchmark: Poisson arrivals over 16 patients, served "
+                         "(batching, overlap, graphs) against one scan at a time")
+    ap.add_argument("--requests", type=int, default=64, help="--serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=20.0, help="--serving: mean arrivals per second")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run only the projector pair on the workload (for profiler captures)")
     return ap.parse_args()
@@ -448,10 +453,162 @@ def run_kernels_only(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# request stream (serving)
+# --------------------------------------------------------------------------
+def serving_patients(n_patients=16, seed=4):
+    """Seeded patient mix: volumes 128^3 / 256^3 / 384^3 (1 mm), 30-120 views
+    (200 or 360 deg), square detectors 256-768 pixels sized to cover the
+    volume, 20-40 iterations (2-4 cycles of 10)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pats = []
+    for k in range(n_patients):
+        n = int(rng.choice([128, 256, 384]))
+        views = int(rng.integers(30, 121))
+        det = int(rng.choice([256, 384, 512, 640, 768]))
+        arc = float(rng.choice([200.0, 360.0]))
+        du = 1.1 * n * 1.0 * 1.5 / det  # magnification 1.5, 10 % margin
+        g = P.Geometry(n, n, n, 1.0, 1.0, 1.0, det, det, du, du, 1000.0, 1500.0,
+                       P.scan_angles(views, arc))
+        pats.append(dict(geometry=g, n_outer=int(rng.integers(2, 5)), n_inner=10, seed=100 + k))
+    return pats
+
+
+def _voxelize_gpu(phantom, g, torch):
+    """Ellipsoid phantom sampled at voxel centres on the GPU (input synthesis)."""
+    vol = torch.zeros((g.nx, g.ny, g.nz), dtype=torch.float32, device="cuda")
+    ax = [((torch.arange(n, device="cuda", dtype=torch.float32) + 0.5) - n / 2.0) * v
+          for n, v in ((g.nx, g.vx), (g.ny, g.vy), (g.nz, g.vz))]
+    X, Y, Z = torch.meshgrid(*ax, indexing="ij")
+    for e in phantom:
+        c = [float(t) for t in e.center]
+        R = torch.tensor(e.rot, dtype=torch.float32, device="cuda")
+        q = torch.zeros_like(X)
+        for a in range(3):
+            qa = ((X - c[0]) * R[0, a] + (Y - c[1]) * R[1, a] + (Z - c[2]) * R[2, a]) / float(e.semi[a])
+            q += qa * qa
+        vol += float(e.mu) * (q <= 1.0).float()
+    return vol
+
+
+def run_serving(args):
+    import threading
+    import torch
+    import paper_2509_08574_gb300 as pk
+
+    pats = serving_patients()
+    t_in = time.perf_counter()
+    data = []
+    for p in pats:
+        g = p["geometry"]
+        prior_ph = P.ellipsoid_phantom(g, 12, seed=p["seed"], body_mu=0.02)
+        change = P.Ellipsoid(np.array([0.1, -0.05, 0.0]) * g.nx, np.array([4.0, 4.0, 4.0]),
+                             np.eye(3), 0.01)
+        xp = _voxelize_gpu(prior_ph, g, torch)
+        xt = xp + _voxelize_gpu([change], g, torch)
+        with pk.Context(g) as ctx:
+            li = ctx.forward(xt)
+        gen = torch.Generator(device="cuda").manual_seed(p["seed"])
+        counts = torch.poisson(5e4 * torch.exp(-li), generator=gen)
+        b = -torch.log(torch.clamp(counts, min=1.0) / 5e4)
+        data.append(dict(prior=xp.cpu().numpy(), proj=b.cpu().pin_memory(),
+                         params=pk.make_params(0.5, 0.5, 1e-2, p["n_outer"], p["n_inner"],
+                                               solver=SOLVERS[args.solver][0])))
+        del xp, xt, li, counts, b
+    torch.cuda.synchronize()
+    t_in = time.perf_counter() - t_in
+    rng = np.random.Generator(np.random.PCG64(9))
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.requests))
+    who = rng.integers(0, len(pats), size=args.requests)
+
+    def outbufs():
+        return [[torch.empty(p["geometry"].vol_shape(), dtype=torch.float32).pin_memory()
+                 for _ in range(2)] for p in pats]
+
+    # plain: one scan at a time in arrival order, sessions resident, no batching
+    outs = outbufs()
+    ctxs = []
+    for p, d in zip(pats, data):
+        c = pk.Context(p["geometry"])
+        c.set_prior(torch.from_numpy(d["prior"]).cuda())
+        ctxs.append(c)
+    for k in range(len(pats)):  # warm the path once per patient
+        ctxs[k].reconstruct_host(data[k]["proj"], data[k]["params"], out=outs[k][0])
+    lat_plain = []
+    t0 = time.perf_counter()
+    for r in range(args.requests):
+        now = time.perf_counter() - t0
+        if now < arrivals[r]:
+            time.sleep(arrivals[r] - now)
+        k = int(who[r])
+        ctxs[k].reconstruct_host(data[k]["proj"], data[k]["params"], out=outs[k][r % 2])
+        lat_plain.append((time.perf_counter() - t0 - arrivals[r]) * 1e3)
+    span_plain = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    torch.cuda.synchronize()
+
+    # served: the request loop
+    outs = outbufs()
+    srv = pk.Server(max_batch=8, max_running=4, use_graphs=True)
+    for k, (p, d) in enumerate(zip(pats, data)):
+        srv.add_patient(k, p["geometry"], d["prior"])
+    for k in range(len(pats)):  # warm: sessions resident, graphs captured for batch 1
+        t, _ = srv.submit(k, data[k]["proj"], data[k]["params"], out=outs[k][0])
+        srv.wait(t)
+    tickets = [None] * args.requests
+    t0 = time.perf_counter()
+
+    def feeder():
+        for r in range(args.requests):
+            now = time.perf_counter() - t0
+            if now < arrivals[r]:
+                time.sleep(arrivals[r] - now)
+            k = int(who[r])
+            tickets[r] = srv.submit(k, data[k]["proj"], data[k]["params"], out=outs[k][r % 2])[0]
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    st = [srv.wait(t) for t in tickets]
+    span_served = time.perf_counter() - t0
+    sstats = srv.stats()
+    srv.close()
+    if any(x["status"] != 0 for x in st):
+        raise RuntimeError("served request failed")
+    lat_served = [x["total_ms"] for x in st]
+
+    def summary(lat, span):
+        return {"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99),
+                "scans_per_s": args.requests / span, "makespan_s": span}
+
+    served, plain = summary(lat_served, span_served), summary(lat_plain, span_plain)
+    line = {
+        "metric": "serving latency p50/p99 and scans/s (Poisson request stream, 16 patients)",
+        "value": served["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.requests} requests, Poisson arrivals {args.rate:g}/s over "
+                               f"{len(pats)} patients: 128^3/256^3/384^3 x 1 mm volumes, 30-120 "
+                               "views, 256^2-768^2 detectors, 20-40 iterations",
+                   "solver": args.solver,
+                   "patients": [[p["geometry"].nx, p["geometry"].n_views, p["geometry"].nu,
+                                 p["n_outer"] * p["n_inner"]] for p in pats]},
+        "served": dict(served, max_batch=8, max_running=4, graphs=True,
+                       mean_batch=args.requests / max(sstats["batches"], 1) if sstats["batches"]
+                       else None, server=sstats),
+        "plain_one_at_a_time": plain,
+        "input_generation_s": t_in,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.kernels_only:
         return run_kernels_only(args)
+    if args.serving:
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
