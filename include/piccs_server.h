@@ -16,6 +16,10 @@
  *     it that share parameters (up to max_batch) are reconstructed together,
  *     one launch per kernel for all of them; requests arriving meanwhile join
  *     the next batch;
+ *   - order: among idle sessions with queued requests, the one whose oldest
+ *     request has the highest response ratio (time waited + estimated device
+ *     time) / estimated device time goes first, so short scans overtake long
+ *     ones while no request waits without bound;
  *   - overlap: up to max_running batches (of different patients) are in
  *     flight at once, each on its session's own CUDA stream;
  *   - captured launches: a session records the launch sequence of each

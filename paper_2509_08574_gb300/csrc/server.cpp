@@ -43,6 +43,7 @@ struct Request {
     int status = PICCS_OK;
     int batch = 0;
     bool done = false;
+    double est_ms = 1.0;  // estimated device time of the scan alone
 };
 
 struct Session {
@@ -207,6 +208,16 @@ int make_resident(piccs_server *srv, Session &s, const piccs_params &params)
     return PICCS_OK;
 }
 
+// Device time of one scan, from its size: every iteration projects each ray
+// through about (nx + ny) / 2 voxels twice (A and A^T, ~1.2e9 pieces per ms)
+// and streams the volume's vectors a few times (~20 pieces' worth per voxel).
+double estimate_ms(const piccs_geometry &g, const piccs_params &p)
+{
+    const double N = (double)g.n_views * g.nu * g.nv, M = (double)g.nx * g.ny * g.nz;
+    const double its = (double)p.n_outer * (p.n_inner > 0 ? p.n_inner : 0) + 1.0;
+    return its * (N * (g.nx + g.ny) + 20.0 * M) / 1.2e9;
+}
+
 bool same_params(const piccs_params &a, const piccs_params &b)
 {
     return std::memcmp(&a, &b, sizeof a) == 0;
@@ -306,20 +317,33 @@ void worker_main(piccs_server *srv)
             s.geo.angles_rad = s.angles.data();
             s.prior = std::move(pp.prior);
         }
-        for (Request *r : arrived) srv->sessions[r->patient].queue.push_back(r);
+        for (Request *r : arrived) {
+            Session &s = srv->sessions[r->patient];
+            r->est_ms = estimate_ms(s.geo, r->params);
+            s.queue.push_back(r);
+        }
         for (Session *s : finished) collect(srv, *s);
 
-        // issue: sessions whose oldest request waits longest go first
+        // issue: highest response ratio (waited + estimated run) / estimated
+        // run first -- short scans go ahead of long ones, and a long scan's
+        // ratio grows while it waits, so none waits without bound
         int running = 0;
         for (auto &kv : srv->sessions) running += !kv.second.running.empty();
         bool progress = true;
         while (progress && running < srv->cfg.max_running) {
             progress = false;
             Session *best = nullptr;
+            double best_ratio = -1.0;
+            const auto now = Clock::now();
             for (auto &kv : srv->sessions) {
                 Session &s = kv.second;
                 if (!s.running.empty() || s.queue.empty()) continue;
-                if (!best || s.queue.front()->id < best->queue.front()->id) best = &s;
+                const Request *h = s.queue.front();
+                const double ratio = (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms;
+                if (ratio > best_ratio) {
+                    best_ratio = ratio;
+                    best = &s;
+                }
             }
             if (!best) break;
             if (issue_batch(srv, *best)) {
