@@ -12,8 +12,11 @@
 // and the right-hand side block is c = lambda^2 D^T W2^2 D x_p.  So the solver
 // never stores the 6M augmented rows; each application is one 7-point stencil
 // pass.  All kernels are memory-bound streaming passes over z-fastest volumes:
-// consecutive threads take consecutive z, the +-1 and +-nz neighbours come
-// from L1 and the +-ny*nz neighbours from L2.
+// blocks stride over the xy voxel columns and the threads of a block run
+// along z, so no voxel index is ever divided; the +-1 and +-nz neighbours
+// come from L1 and the +-ny*nz neighbours from L2.  Sums are kept per thread
+// in compensated FP32 and combined in FP64 per block (FP64 arithmetic per
+// voxel would cost more than the memory traffic on this GPU).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -25,13 +28,47 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void unflatten(long long i, int ny, int nz, int &ix, int &iy, int &iz)
+// Visits every voxel once.  The threads of a block form groups of nzr (nz
+// rounded up to whole warps, at most the block), one xy column (ix * ny + iy)
+// per group; the block's groups take consecutive columns and the grid strides
+// over them, stepping (ix, iy) without division.  f(i, ix, iy, iz), i the flat
+// index.
+template <class F>
+__device__ __forceinline__ void for_voxels(const VolDims &d, F &&f)
 {
-    iz = (int)(i % nz);
-    const long long t = i / nz;
-    iy = (int)(t % ny);
-    ix = (int)(t / ny);
+    const int nzr = min((d.nz + 31) / 32 * 32, (int)blockDim.x);
+    const int cpi = (int)blockDim.x / nzr;
+    const int sub = (int)threadIdx.x / nzr, tz = (int)threadIdx.x - sub * nzr;
+    if (sub >= cpi) return;
+    const int ncol = d.nx * d.ny;  // < 2^31 (the volume is)
+    const int step = (int)gridDim.x * cpi;
+    const int step_x = step / d.ny, step_y = step - step_x * d.ny;
+    int col = (int)blockIdx.x * cpi + sub;
+    int ix = col / d.ny, iy = col - ix * d.ny;
+    for (; col < ncol; col += step) {
+        const long long base = (long long)col * d.nz;
+        for (int iz = tz; iz < d.nz; iz += nzr) f(base + iz, ix, iy, iz);
+        ix += step_x;
+        iy += step_y;
+        if (iy >= d.ny) {
+            iy -= d.ny;
+            ++ix;
+        }
+    }
 }
+
+// Compensated (Kahan) FP32 sum of one thread's terms.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // w^2 for a gradient with squared Euclidean norm n2 (tau2 = tau^2):
 // R1 1/(|g| + tau^2), R2 1/sqrt(|g|^2 + tau^2)
@@ -52,10 +89,8 @@ weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float 
     omega = slot_ptr(omega, so);
     w2sq = slot_ptr(w2sq, so);
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        unflatten(i, d.ny, d.nz, ix, iy, iz);
+    (void)M;
+    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
         const float xi = x[i];
         const float gx = (ix + 1 < d.nx) ? xi - x[i + sx] : 0.f;
         const float gy = (iy + 1 < d.ny) ? xi - x[i + sy] : 0.f;
@@ -72,7 +107,7 @@ weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float 
             w2sq[i] = w2;
         }
         omega[i] = om;
-    }
+    });
 }
 
 // c = lambda^2 D^T W2^2 D x_p (PICCS), lambda^2 x_p (PIPLE), 0 otherwise
@@ -86,12 +121,10 @@ prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
     w2sq = slot_ptr(w2sq, so);
     c = slot_ptr(c, so);
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
+    (void)M;
+    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
         float out = 0.f;
         if (variant == 0) {
-            int ix, iy, iz;
-            unflatten(i, d.ny, d.nz, ix, iy, iz);
             const float pi = xp[i], wi = w2sq[i];
             float acc = 0.f;
             if (ix + 1 < d.nx) acc += wi * (pi - xp[i + sx]);
@@ -105,17 +138,16 @@ prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
             out = lambda2 * xp[i];
         }
         c[i] = out;
-    }
+    });
 }
 
 // t = D^T diag(omega) D z (+ lam2 z) at voxel i, and omega |(Dz)_i|^2 (+ lam2 z_i^2)
-__device__ __forceinline__ float stencil_at(VolDims d, long long i, const float *__restrict__ z,
+__device__ __forceinline__ float stencil_at(const VolDims &d, long long i, int ix, int iy, int iz,
+                                            const float *__restrict__ z,
                                             const float *__restrict__ omega, float lam2,
                                             float &energy)
 {
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
-    int ix, iy, iz;
-    unflatten(i, d.ny, d.nz, ix, iy, iz);
     const float zi = z[i];
     const float w = omega[i];
     const float gx = (ix + 1 < d.nx) ? zi - z[i + sx] : 0.f;
@@ -156,14 +188,14 @@ reg_normal_kernel(VolDims d, long long M, const float *__restrict__ z,
     omega = slot_ptr(omega, so);
     out = slot_ptr(out, so);
     partials = slot_ptr(partials, so);
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
+    KahanF acc;
+    (void)M;
+    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
         float e;
-        out[i] = stencil_at(d, i, z, omega, lam2, e);
-        acc += (double)e;
-    }
-    if (NORM) block_sum_store(acc, partials);
+        out[i] = stencil_at(d, i, ix, iy, iz, z, omega, lam2, e);
+        if (NORM) acc.add(e);
+    });
+    if (NORM) block_sum_store(acc.value(), partials);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -179,22 +211,17 @@ reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
     g = slot_ptr(g, so);
     s = slot_ptr(s, so);
     partials = slot_ptr(partials, so);
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
+    KahanF acc;
+    (void)M;
+    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
         float e;
-        const float gn = c[i] - stencil_at(d, i, x, omega, lam2, e);
-        float sn;
-        if (first) {
-            sn = gn;
-        } else {
-            sn = s[i] + (gn - g[i]);
-        }
+        const float gn = c[i] - stencil_at(d, i, ix, iy, iz, x, omega, lam2, e);
+        const float sn = first ? gn : s[i] + (gn - g[i]);
         g[i] = gn;
         s[i] = sn;
-        acc += (double)sn * (double)sn;
-    }
-    if (partials) block_sum_store(acc, partials);
+        acc.add(sn * sn);
+    });
+    if (partials) block_sum_store(acc.value(), partials);
 }
 
 // Block sums of up to three per-thread values, one partial per block each,
@@ -252,11 +279,9 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
     }
     auto zn = [&](long long j) { return INIT ? -src[j] : fmaf(ca, src[j], -cb * zold[j]); };
     const long long sx = (long long)d.ny * d.nz, sy = d.nz;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
-         i += (long long)gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        unflatten(i, d.ny, d.nz, ix, iy, iz);
+    KahanF k0, k1, k2;
+    (void)M;
+    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
         const float zi = zn(i);
         const float w = omega[i];
         const float gx = (ix + 1 < d.nx) ? zi - zn(i + sx) : 0.f;
@@ -270,10 +295,11 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
         const float ci = c[i];
         znew[i] = zi;
         s[i] = fmaf(sig, ci, t);
-        acc[0] += (double)(w * (gx * gx + gy * gy + gz * gz) + lam2 * zi * zi);
-        acc[1] += (double)(zi * ci);
-        if (INIT && xp) acc[2] += (double)(xp[i] * ci);  // |b_R|^2 (no prior: b_R = 0)
-    }
+        k0.add(w * (gx * gx + gy * gy + gz * gz) + lam2 * zi * zi);
+        k1.add(zi * ci);
+        if (INIT && xp) k2.add(xp[i] * ci);  // |b_R|^2 (no prior: b_R = 0)
+    });
+    const double acc[3] = {k0.value(), k1.value(), k2.value()};
     if (INIT) {
         block_sums_store<3>(acc, partials);
     } else {
