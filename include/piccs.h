@@ -82,6 +82,15 @@ enum { PICCS_X0_PRIOR = 0, PICCS_X0_ZERO = 1, PICCS_X0_USER = 2 };
  * them) and keeps them; n_inner - 1 must not exceed 256. */
 enum { PICCS_SOLVER_CGLS = 0, PICCS_SOLVER_LSQR = 1, PICCS_SOLVER_LSQR_REORTH = 2 };
 
+/* Storage precision.  F32: every vector in FP32.  BF16: the measured
+ * projections b, the backprojection's per-ray values (the residual scaled by
+ * the ray's secant) and the LSQR re-orthogonalisation basis are held in BF16
+ * (rounded to nearest even once, when stored); rays still accumulate in FP32,
+ * the recurrence vectors (residuals, search directions, iterates) stay FP32
+ * and every inner product and Krylov scalar is FP64.  FP32 input is rounded
+ * on the device; piccs_stage_bf16 takes BF16 data directly. */
+enum { PICCS_STORAGE_F32 = 0, PICCS_STORAGE_BF16 = 1 };
+
 typedef struct {
     int nx, ny, nz;            /* voxels */
     double vx, vy, vz;         /* voxel size, mm (> 0) */
@@ -105,6 +114,7 @@ typedef struct {
     int variant;               /* PICCS_VARIANT_* */
     int weight_rule;           /* PICCS_WEIGHT_* */
     int solver;                /* PICCS_SOLVER_* */
+    int storage;               /* PICCS_STORAGE_* */
 } piccs_params;
 
 /* What the last reconstruction did (filled by piccs_report, which waits). */
@@ -214,10 +224,12 @@ int piccs_report_slot(piccs_ctx *ctx, int slot, piccs_stats *out);
  * `slot`'s volume out.  All three are asynchronous on the context's stream
  * (host buffers should be pinned).  use_graph != 0: the launch sequence of a
  * (params, nactive) pair is captured once as a CUDA graph and replayed (the
- * per-step scalars stay on the device, so a replay is a full reconstruction);
- * the first run of each pair synchronises for the capture. */
+ * per-step scalars stay on the device, so a replay is a full reconstruction). */
 int piccs_set_prior_broadcast(piccs_ctx *ctx, const float *xprior, int from_host);
 int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host);
+/* The same with projections already in BF16 (N values, bfloat16 bit
+ * patterns); the run must then use PICCS_STORAGE_BF16. */
+int piccs_stage_bf16(piccs_ctx *ctx, int slot, const void *proj, int from_host);
 int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph);
 int piccs_unstage(piccs_ctx *ctx, int slot, float *vol, int to_host);
 

@@ -85,11 +85,13 @@ int piccs_server_add_patient(piccs_server *srv, int patient, const piccs_geometr
                              const float *h_xprior);
 
 /* Queue a reconstruction of patient `patient` (x0_mode PRIOR or ZERO).
- * h_proj (N floats) is read and h_out (M floats) written asynchronously, so
+ * h_proj holds N projection values: FP32, or BF16 bit patterns when
+ * params->storage is PICCS_STORAGE_BF16 (half the bytes to move).
+ * h_proj is read and h_out (M floats) written asynchronously, so
  * both must stay valid, and h_proj unchanged, until piccs_server_wait reports
  * the request done; pinned host memory lets the copies overlap.  Returns at
  * once with the request's ticket. */
-int piccs_server_submit(piccs_server *srv, int patient, const float *h_proj,
+int piccs_server_submit(piccs_server *srv, int patient, const void *h_proj,
                         const piccs_params *params, float *h_out, long long *ticket);
 
 /* Wait for a request (timeout_ms < 0: without limit).  PICCS_ETIMEOUT if it

@@ -31,6 +31,7 @@ VARIANT_PICCS, VARIANT_PIPLE, VARIANT_TV, VARIANT_CGLS = 0, 1, 2, 3
 WEIGHT_R1, WEIGHT_R2 = 0, 1
 X0_PRIOR, X0_ZERO, X0_USER = 0, 1, 2
 SOLVER_CGLS, SOLVER_LSQR, SOLVER_LSQR_REORTH = 0, 1, 2
+STORAGE_F32, STORAGE_BF16 = 0, 1
 
 _NAMES = {0: "PICCS_OK", -1: "PICCS_EINVAL", -2: "PICCS_ENOMEM", -3: "PICCS_ENONFINITE",
           -4: "PICCS_EBREAKDOWN", -5: "PICCS_ETIMEOUT", -6: "PICCS_ECUDA", -7: "PICCS_ENOTIMPL"}
@@ -55,7 +56,8 @@ class piccs_geometry(C.Structure):
 class piccs_params(C.Structure):
     _fields_ = [("alpha", C.c_float), ("lambda_", C.c_float), ("tau", C.c_float),
                 ("n_outer", C.c_int), ("n_inner", C.c_int), ("x0_mode", C.c_int),
-                ("variant", C.c_int), ("weight_rule", C.c_int), ("solver", C.c_int)]
+                ("variant", C.c_int), ("weight_rule", C.c_int), ("solver", C.c_int),
+                ("storage", C.c_int)]
 
 
 class piccs_stats(C.Structure):
@@ -102,6 +104,7 @@ def _load():
         "piccs_report_slot": (i, [vp, i, R]),
         "piccs_set_prior_broadcast": (i, [vp, vp, i]),
         "piccs_stage": (i, [vp, i, vp, i]),
+        "piccs_stage_bf16": (i, [vp, i, vp, i]),
         "piccs_run_staged": (i, [vp, i, P, i]),
         "piccs_unstage": (i, [vp, i, vp, i]),
         "piccs_server_create": (i, [C.POINTER(vp), C.POINTER(piccs_server_config)]),
@@ -142,7 +145,7 @@ EXPORTED = ("piccs_create", "piccs_destroy", "piccs_last_error", "piccs_set_stre
             "piccs_reg_weights", "piccs_reg_normal", "piccs_profile_enable",
             "piccs_profile_read", "piccs_reg_normal_noalloc", "piccs_create_batched",
             "piccs_query_workspace_batched", "piccs_report_slot", "piccs_set_prior_broadcast",
-            "piccs_stage", "piccs_run_staged", "piccs_unstage", "piccs_server_create",
+            "piccs_stage", "piccs_stage_bf16", "piccs_run_staged", "piccs_unstage", "piccs_server_create",
             "piccs_server_destroy", "piccs_server_last_error", "piccs_server_add_patient",
             "piccs_server_submit", "piccs_server_wait", "piccs_server_get_stats")
 
@@ -178,6 +181,22 @@ def _ptr(t, n=None, what="buffer"):
     raise TypeError(f"{what}: unsupported type {type(t)}")
 
 
+def _ptr16(t, n, what="buffer"):
+    """Pointer of a contiguous BF16 buffer (torch.bfloat16 / int16 tensor or
+    uint16 numpy array of bit patterns) of n elements."""
+    if hasattr(t, "data_ptr"):
+        if str(t.dtype) not in ("torch.bfloat16", "torch.int16", "torch.uint16"):
+            raise TypeError(f"{what} must be bfloat16, got {t.dtype}")
+        if not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{what} must be contiguous with {n} elements")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if t.dtype not in (np.uint16, np.int16) or not t.flags.c_contiguous or t.size != n:
+            raise TypeError(f"{what} must be a contiguous uint16 array of {n} elements")
+        return t.ctypes.data
+    raise TypeError(f"{what}: unsupported type {type(t)}")
+
+
 def _check(rc, ctx=None):
     if rc != PICCS_OK:
         msg = _lib.piccs_last_error(ctx)
@@ -198,8 +217,10 @@ def make_geometry(g):
 
 
 def make_params(alpha=0.5, lam=0.5, tau=1e-2, n_outer=1, n_inner=10, x0_mode=X0_PRIOR,
-                variant=VARIANT_PICCS, weight_rule=WEIGHT_R1, solver=SOLVER_CGLS):
-    return piccs_params(alpha, lam, tau, n_outer, n_inner, x0_mode, variant, weight_rule, solver)
+                variant=VARIANT_PICCS, weight_rule=WEIGHT_R1, solver=SOLVER_CGLS,
+                storage=STORAGE_F32):
+    return piccs_params(alpha, lam, tau, n_outer, n_inner, x0_mode, variant, weight_rule, solver,
+                        storage)
 
 
 def _stream_handle(stream):
@@ -428,6 +449,27 @@ class Context:
     def report(self, slot=0):
         return piccs_report_slot(self.h, slot)
 
+    # staged reconstructions (the request server's building blocks)
+    def set_prior_broadcast(self, prior_host):
+        prior_host = np.ascontiguousarray(prior_host, dtype=np.float32)
+        _check(_lib.piccs_set_prior_broadcast(self.h, _ptr(prior_host, self.M, "prior"), 1), self.h)
+
+    def stage(self, slot, proj, host=True):
+        _check(_lib.piccs_stage(self.h, int(slot), _ptr(proj, self.N, "projections"),
+                                1 if host else 0), self.h)
+
+    def stage_bf16(self, slot, proj_bits, host=True):
+        _check(_lib.piccs_stage_bf16(self.h, int(slot), _ptr16(proj_bits, self.N, "projections"),
+                                     1 if host else 0), self.h)
+
+    def run_staged(self, nactive, params, graph=True):
+        _check(_lib.piccs_run_staged(self.h, int(nactive), C.byref(params), 1 if graph else 0),
+               self.h)
+
+    def unstage(self, slot, out, host=True):
+        _check(_lib.piccs_unstage(self.h, int(slot), _ptr(out, self.M, "volume"),
+                                  1 if host else 0), self.h)
+
     def profile_enable(self, timing=True):
         piccs_profile_enable(self.h, timing)
 
@@ -498,13 +540,16 @@ class Server:
         self._shapes[int(patient)] = (gs.n_views * gs.nu * gs.nv, (gs.nx, gs.ny, gs.nz))
 
     def submit(self, patient, proj, params, out=None):
-        """proj: host projections (pinned torch tensor or numpy array); returns
-        (ticket, out)."""
+        """proj: host projections (pinned torch tensor or numpy array; BF16 --
+        torch.bfloat16 or uint16 bit patterns -- for STORAGE_BF16 params);
+        returns (ticket, out)."""
         N, vol_shape = self._shapes[int(patient)]
         if out is None:
             out = np.empty(vol_shape, dtype=np.float32)
         t = C.c_longlong(0)
-        _check_srv(_lib.piccs_server_submit(self.h, int(patient), _ptr(proj, N, "projections"),
+        pp = _ptr16(proj, N, "projections") if params.storage == STORAGE_BF16 else \
+            _ptr(proj, N, "projections")
+        _check_srv(_lib.piccs_server_submit(self.h, int(patient), pp,
                                             C.byref(params), _ptr(out, int(np.prod(vol_shape)),
                                                                   "volume"), C.byref(t)), self.h)
         self._held[t.value] = (proj, out, params)

@@ -110,22 +110,28 @@ struct LsqrScalars {
     double h[kMaxBasis];  // Gram-Schmidt coefficients
 };
 
-enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_LSQR = 2 };
+enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_LSQR = 2, FWD_RESID16 = 3 };
 
 // ---- projector (kernels_project.cu) ----
 int project_blocks(const ProjGeom &g);
 // vr[iv] = {v, 1/v} per detector row (1e30 for v = 0)
 // mode FWD_PLAIN: out = A vol; FWD_RESID: out = aux - A vol (aux = the data b,
-// NaN/Inf in it set *nonfinite).  partials (may be null) get |out|^2 per block.
+// NaN/Inf in it set *nonfinite); FWD_RESID16: the same with b in BF16.
+// partials (may be null) get |out|^2 per block.
 cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int4 *cells, const float *vol, float *out, int mode,
                            const float *aux, double *partials, int *nonfinite, cudaStream_t st,
                            Slots sl = Slots{1, 0});
 // vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
-// N-float scratch that receives proj scaled by each ray's sec.
+// N-float scratch that receives proj scaled by each ray's sec (rounded to
+// BF16, N of them, when rs_bf16).
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st, Slots sl = Slots{1, 0});
+                           float *vol, cudaStream_t st, Slots sl = Slots{1, 0},
+                           bool rs_bf16 = false);
+// n FP32 values per slot -> BF16 (round to nearest even)
+cudaError_t launch_to_bf16(long long n, const float *src, long long src_stride, void *dst,
+                           long long dst_stride, int nslot, cudaStream_t st);
 
 // LSQR u-step with the data residual kept current (aux = LsqrScalars::fwd):
 // q = aux[0] A vol; U = q - aux[1] U; first step of a cycle (aux[5]): Aw = q;
@@ -182,6 +188,9 @@ cudaError_t launch_finalize_gamma(KrylovScalars *k, const double *p, int n, int 
 cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st, Slots sl = Slots{1, 0});
 cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st,
                                    Slots sl = Slots{1, 0});
+// the same for n BF16 values
+cudaError_t launch_count_nonfinite16(long long n, const void *v, int *flag, cudaStream_t st,
+                                     Slots sl = Slots{1, 0});
 cudaError_t launch_sum_partials(const double *p, int n, double *out, cudaStream_t st);
 // LSQR
 cudaError_t launch_lsqr_reset(KrylovScalars *k, LsqrScalars *l, cudaStream_t st,
@@ -195,8 +204,9 @@ cudaError_t launch_lsqr_rinit(long long N, int update, float *rA, const float *A
 // unless last, vhat = s / beta_{i+1} - beta_{i+1} v; basis (may be null) gets v.
 // partials get |vhat|^2 (unless last).
 cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
-                           const float *s, float *basis, const LsqrScalars *l, double *partials,
-                           cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0);
+                           const float *s, void *basis, const LsqrScalars *l, double *partials,
+                           cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0,
+                           bool basis_bf16 = false);
 // beta = sqrt(|uA|^2 + z.Kz + 2 sigma <z,c> + sigma^2 |b_R|^2) and the Givens step
 cudaError_t launch_lsqr_finalize_beta(KrylovScalars *k, LsqrScalars *l, int init,
                                       const double *pu, int nu, const double *pr, int nr,
@@ -212,14 +222,15 @@ inline long long lsqr_basis_stride(long long M) { return (M + 63) / 64 * 64; }
 // dots: partials[j * lsqr_dot_blocks() + block] = <basis_j, vhat>;
 // fin_dots: l->h[j] = their fixed-order sums; sub: vhat -= sum_j h_j basis_j,
 // norm_partials (may be null) get |vhat|^2.  All skip once l->stopped.
-cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
+cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const void *basis,
                              const float *vhat, const LsqrScalars *l, double *partials,
-                             cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0);
+                             cudaStream_t st, Slots sl = Slots{1, 0}, long long bstride = 0,
+                             bool basis_bf16 = false);
 cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials, cudaStream_t st,
                                  Slots sl = Slots{1, 0}, long long bstride = 0);
-cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
+cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const void *basis, float *vhat,
                             const LsqrScalars *l, double *norm_partials, cudaStream_t st,
-                            Slots sl = Slots{1, 0}, long long bstride = 0);
+                            Slots sl = Slots{1, 0}, long long bstride = 0, bool basis_bf16 = false);
 int lsqr_dot_blocks();
 
 // ---- host helpers (piccs_api.cpp) ----

@@ -8,6 +8,7 @@
 // iteration sequence without a host round trip.  Reductions are two-level and
 // deterministic: each kernel writes one FP64 partial per CTA, and a one-CTA
 // finalize kernel adds the partials in a fixed order.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -19,6 +20,37 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kFinThreads = 1024;
+
+// Four consecutive basis values (FP32, or BF16 when stored at reduced
+// precision), i counted in groups of four.
+__device__ __forceinline__ float4 ld4(const float *p, long long i)
+{
+    return reinterpret_cast<const float4 *>(p)[i];
+}
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p, long long i)
+{
+    const uint2 u = reinterpret_cast<const uint2 *>(p)[i];
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ void st4(float *p, long long i, float4 v)
+{
+    reinterpret_cast<float4 *>(p)[i] = v;
+}
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, long long i, float4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    reinterpret_cast<uint2 *>(p)[i] = u;
+}
+__device__ __forceinline__ float ld1(const float *p, long long i) { return p[i]; }
+__device__ __forceinline__ float ld1(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void st1(float *p, long long i, float v) { p[i] = v; }
+__device__ __forceinline__ void st1(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
 
 __global__ void __launch_bounds__(kThreads)
 p_update_kernel(long long M, const float *__restrict__ s, float *__restrict__ p,
@@ -311,10 +343,10 @@ lsqr_rinit_kernel(long long N, int update, float *__restrict__ ra, const float *
     block_sum_store(acc, partials);
 }
 
-template <bool FIRST, bool LAST>
+template <bool FIRST, bool LAST, class BT>
 __global__ void __launch_bounds__(kThreads)
 lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
-               float *__restrict__ vhat, const float *__restrict__ s, float *__restrict__ basis,
+               float *__restrict__ vhat, const float *__restrict__ s, BT *__restrict__ basis,
                const LsqrScalars *__restrict__ l, double *__restrict__ partials, long long sstride,
                long long bstride)
 {
@@ -353,7 +385,6 @@ lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
     float4 *x4 = reinterpret_cast<float4 *>(x);
     float4 *w4 = reinterpret_cast<float4 *>(w);
     float4 *v4 = reinterpret_cast<float4 *>(vhat);
-    float4 *b4 = reinterpret_cast<float4 *>(basis);
     for (long long i = t0; i < n4; i += stride) {
         const float4 si = LAST ? make_float4(0.f, 0.f, 0.f, 0.f) : s4[i];
         float4 vh = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : v4[i];
@@ -370,7 +401,7 @@ lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
         if (!FIRST) {
             x4[i] = xo;
             w4[i] = wo;
-            if (basis) b4[i] = bo;
+            if (basis) st4(basis, i, bo);
         }
         if (!LAST) v4[i] = vo;
     }
@@ -381,7 +412,7 @@ lsqr_vx_kernel(long long M, float *__restrict__ x, float *__restrict__ w,
         if (!FIRST) {
             x[i] = xo;
             w[i] = wo;
-            if (basis) basis[i] = bo;
+            if (basis) st1(basis, i, bo);
         }
         if (!LAST) vhat[i] = vo;
     }
@@ -503,8 +534,9 @@ lsqr_finalize_alpha_kernel(KrylovScalars *k, LsqrScalars *l, int init, const dou
 // blockIdx.y; one FP64 partial per (j, block) at partials[j * gridDim.x + block]
 constexpr int kDotVecs = 8;
 
+template <class BT>
 __global__ void __launch_bounds__(kThreads)
-lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
+lsqr_dots_kernel(long long M, long long ldb, int nb, const BT *__restrict__ basis,
                  const float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
                  double *__restrict__ partials, long long sstride, long long bstride)
 {
@@ -530,7 +562,7 @@ lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ b
 #pragma unroll
         for (int q = 0; q < kDotVecs; ++q) {
             if (q < nj) {
-                const float4 b = reinterpret_cast<const float4 *>(basis + (long long)(j0 + q) * ldb)[i];
+                const float4 b = ld4(basis + (long long)(j0 + q) * ldb, i);
                 acc[q] += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
             }
         }
@@ -538,7 +570,7 @@ lsqr_dots_kernel(long long M, long long ldb, int nb, const float *__restrict__ b
     for (long long i = (n4 << 2) + t0; i < M; i += stride) {
 #pragma unroll
         for (int q = 0; q < kDotVecs; ++q)
-            if (q < nj) acc[q] += (double)vhat[i] * (double)basis[(long long)(j0 + q) * ldb + i];
+            if (q < nj) acc[q] += (double)vhat[i] * (double)ld1(basis + (long long)(j0 + q) * ldb, i);
     }
     __shared__ double red[kDotVecs][kThreads / 32];
 #pragma unroll
@@ -568,8 +600,9 @@ lsqr_fin_dots_kernel(LsqrScalars *l, const double *partials, int nblk, long long
 }
 
 // vhat -= sum_j h_j basis_j; partials (may be null) get |vhat|^2
+template <class BT>
 __global__ void __launch_bounds__(kThreads)
-lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ basis,
+lsqr_sub_kernel(long long M, long long ldb, int nb, const BT *__restrict__ basis,
                 float *__restrict__ vhat, const LsqrScalars *__restrict__ l,
                 double *__restrict__ partials, long long sstride, long long bstride)
 {
@@ -590,7 +623,7 @@ lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ ba
         float4 a = v4[i];
         for (int j = 0; j < nb; ++j) {
             const float h = (float)l->h[j];
-            const float4 b = reinterpret_cast<const float4 *>(basis + (long long)j * ldb)[i];
+            const float4 b = ld4(basis + (long long)j * ldb, i);
             a.x = fmaf(-h, b.x, a.x);
             a.y = fmaf(-h, b.y, a.y);
             a.z = fmaf(-h, b.z, a.z);
@@ -601,7 +634,7 @@ lsqr_sub_kernel(long long M, long long ldb, int nb, const float *__restrict__ ba
     }
     for (long long i = (n4 << 2) + t0; i < M; i += stride) {
         float a = vhat[i];
-        for (int j = 0; j < nb; ++j) a = fmaf(-(float)l->h[j], basis[(long long)j * ldb + i], a);
+        for (int j = 0; j < nb; ++j) a = fmaf(-(float)l->h[j], ld1(basis + (long long)j * ldb, i), a);
         vhat[i] = a;
         acc += (double)a * (double)a;
     }
@@ -654,6 +687,28 @@ cudaError_t launch_reset_scalars(KrylovScalars *k, cudaStream_t st, Slots sl)
     return cudaGetLastError();
 }
 
+// BF16 data: NaN/Inf have all exponent bits set
+__global__ void __launch_bounds__(kThreads)
+count_nonfinite16_kernel(long long n, const unsigned short *__restrict__ v, int *__restrict__ flag,
+                         long long sstride)
+{
+    v = slot_ptr(v, blockIdx.y * sstride);
+    flag = slot_ptr(flag, blockIdx.y * sstride);
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= (v[i] & 0x7F80u) == 0x7F80u;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_count_nonfinite16(long long n, const void *v, int *flag, cudaStream_t st,
+                                     Slots sl)
+{
+    count_nonfinite16_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(
+        n, static_cast<const unsigned short *>(v), flag, sl.stride);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count_nonfinite(long long n, const float *v, int *flag, cudaStream_t st,
                                    Slots sl)
 {
@@ -685,19 +740,22 @@ cudaError_t launch_lsqr_reset(KrylovScalars *, LsqrScalars *l, cudaStream_t st, 
 }
 
 cudaError_t launch_lsqr_vx(long long M, int first, int last, float *x, float *w, float *vhat,
-                           const float *s, float *basis, const LsqrScalars *l, double *partials,
-                           cudaStream_t st, Slots sl, long long bstride)
+                           const float *s, void *basis, const LsqrScalars *l, double *partials,
+                           cudaStream_t st, Slots sl, long long bstride, bool basis_bf16)
 {
     const dim3 grid(vector_blocks(), sl.n);
     if (first)
-        lsqr_vx_kernel<true, false><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
-                                                              partials, sl.stride, 0);
+        lsqr_vx_kernel<true, false, float><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
+                                                                     partials, sl.stride, 0);
     else if (last)
-        lsqr_vx_kernel<false, true><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
-                                                              partials, sl.stride, 0);
+        lsqr_vx_kernel<false, true, float><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, nullptr, l,
+                                                                     partials, sl.stride, 0);
+    else if (basis_bf16)
+        lsqr_vx_kernel<false, false, __nv_bfloat16><<<grid, kThreads, 0, st>>>(
+            M, x, w, vhat, s, static_cast<__nv_bfloat16 *>(basis), l, partials, sl.stride, bstride);
     else
-        lsqr_vx_kernel<false, false><<<grid, kThreads, 0, st>>>(M, x, w, vhat, s, basis, l,
-                                                               partials, sl.stride, bstride);
+        lsqr_vx_kernel<false, false, float><<<grid, kThreads, 0, st>>>(
+            M, x, w, vhat, s, static_cast<float *>(basis), l, partials, sl.stride, bstride);
     return cudaGetLastError();
 }
 
@@ -717,14 +775,19 @@ cudaError_t launch_lsqr_finalize_alpha(KrylovScalars *k, LsqrScalars *l, int ini
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const float *basis,
+cudaError_t launch_lsqr_dots(long long M, long long ldb, int nb, const void *basis,
                              const float *vhat, const LsqrScalars *l, double *partials,
-                             cudaStream_t st, Slots sl, long long bstride)
+                             cudaStream_t st, Slots sl, long long bstride, bool basis_bf16)
 {
     const dim3 grid((unsigned)lsqr_dot_blocks(), (unsigned)((nb + kDotVecs - 1) / kDotVecs),
                     (unsigned)sl.n);
-    lsqr_dots_kernel<<<grid, kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l, partials, sl.stride,
-                                                bstride);
+    if (basis_bf16)
+        lsqr_dots_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(
+            M, ldb, nb, static_cast<const __nv_bfloat16 *>(basis), vhat, l, partials, sl.stride,
+            bstride);
+    else
+        lsqr_dots_kernel<float><<<grid, kThreads, 0, st>>>(M, ldb, nb, static_cast<const float *>(basis),
+                                                           vhat, l, partials, sl.stride, bstride);
     return cudaGetLastError();
 }
 
@@ -736,13 +799,18 @@ cudaError_t launch_lsqr_fin_dots(int nb, LsqrScalars *l, const double *partials,
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const float *basis, float *vhat,
+cudaError_t launch_lsqr_sub(long long M, long long ldb, int nb, const void *basis, float *vhat,
                             const LsqrScalars *l, double *norm_partials, cudaStream_t st, Slots sl,
-                            long long bstride)
+                            long long bstride, bool basis_bf16)
 {
-    lsqr_sub_kernel<<<dim3(vector_blocks(), sl.n), kThreads, 0, st>>>(M, ldb, nb, basis, vhat, l,
-                                                                     norm_partials, sl.stride,
-                                                                     bstride);
+    const dim3 grid(vector_blocks(), sl.n);
+    if (basis_bf16)
+        lsqr_sub_kernel<__nv_bfloat16><<<grid, kThreads, 0, st>>>(
+            M, ldb, nb, static_cast<const __nv_bfloat16 *>(basis), vhat, l, norm_partials, sl.stride,
+            bstride);
+    else
+        lsqr_sub_kernel<float><<<grid, kThreads, 0, st>>>(M, ldb, nb, static_cast<const float *>(basis),
+                                                          vhat, l, norm_partials, sl.stride, bstride);
     return cudaGetLastError();
 }
 

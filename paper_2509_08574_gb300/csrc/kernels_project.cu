@@ -30,6 +30,7 @@
 // fma(kc, KD / v, -s0), with the exact plane coordinate kc (never an
 // accumulated distance), so A^T applies bit-identical weights to A; only the
 // order of the FP32 sums differs.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -51,6 +52,12 @@ __device__ __forceinline__ float ray_sec(float v, float invD)
     const float m = v * invD;
     return __fsqrt_rn(fmaf(m, m, 1.f));
 }
+
+// ray values are FP32, or BF16 when the context stores projections in BF16
+__device__ __forceinline__ float ld_ray(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_ray(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ void st_ray(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_ray(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -159,9 +166,16 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         const long long base = (long long)j * G.sj + (long long)iu * G.su;
         const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
         float qa = sec * acca, qb = sec * accb;
-        if (MODE == FWD_RESID) {
-            const float ba = aux[ia];
-            const float bb = has_b ? aux[ib] : 0.f;
+        if (MODE == FWD_RESID || MODE == FWD_RESID16) {
+            float ba, bb;
+            if (MODE == FWD_RESID) {
+                ba = aux[ia];
+                bb = has_b ? aux[ib] : 0.f;
+            } else {
+                const __nv_bfloat16 *b16 = reinterpret_cast<const __nv_bfloat16 *>(aux);
+                ba = __bfloat162float(b16[ia]);
+                bb = has_b ? __bfloat162float(b16[ib]) : 0.f;
+            }
             if (!isfinite(ba) || !isfinite(bb)) atomicOr(nonfinite, 1);
             qa = ba - qa;
             qb = bb - qb;
@@ -211,9 +225,10 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
 }
 
 // rs = proj * sec, per ray (the adjoint's gather then needs no square root)
+template <class RT>
 __global__ void __launch_bounds__(256)
 scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-                  const float *__restrict__ proj, float *__restrict__ rs, long long sstride)
+                  const float *__restrict__ proj, RT *__restrict__ rs, long long sstride)
 {
     proj = slot_ptr(proj, blockIdx.y * sstride);
     rs = slot_ptr(rs, blockIdx.y * sstride);
@@ -225,8 +240,8 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
     const int iva = G.nv - 1 - p;
     const float sec = ray_sec(__ldg(vr + iva).x, cols[col].invD);  // same for the mirror row
     const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
-    rs[ia] = proj[ia] * sec;
-    if (p != iva) rs[ib] = proj[ib] * sec;
+    st_ray(rs + ia, proj[ia] * sec);
+    if (p != iva) st_ray(rs + ib, proj[ib] * sec);
 }
 
 // Adjoint gather: CTA = one xy voxel column (ix, iy), thread = kLayersPerThread
@@ -237,10 +252,11 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // v in [zl, zh] / ((s0 + s) rKD)); each candidate row r is checked with the
 // exact piece length -- the expression the forward walk evaluates -- which is
 // also the length of row nv-1-r in layer p.
+template <class RT>
 __global__ void __launch_bounds__(kGatherThreads)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
-                  const float *__restrict__ rs, float *__restrict__ vol, long long sstride)
+                  const RT *__restrict__ rs, float *__restrict__ vol, long long sstride)
 {
     rs = slot_ptr(rs, blockIdx.z * sstride);
     vol = slot_ptr(vol, blockIdx.z * sstride);
@@ -268,8 +284,8 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
         const float s0 = cz.x, KD = cz.y, rKD = cz.w;
         // candidate bounds only: the rows are then checked exactly
         const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
-        const float *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
-        const float *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
+        const RT *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
+        const RT *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
 #pragma unroll
         for (int q = 0; q < L; ++q) {
             const float zl = zlo[q], zh = zl + 1.f;
@@ -289,9 +305,9 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                 // the ray is inside the layer between its two plane crossings
                 const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
                 if (len > 0.f) {
-                    accu[q] = fmaf(len, __ldg(rsc + iv * G.sv32), accu[q]);
+                    accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
                     if (!mid || 2 * iv != nvm1)
-                        accd[q] = fmaf(len, __ldg(rsm - iv * G.sv32), accd[q]);
+                        accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
                 }
             };
             if (ilo <= ihi) cand(ilo);
@@ -332,6 +348,8 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
                                               nonfinite, nullptr, nullptr, sl.stride)
     if (mode == FWD_RESID) {
         if (partials) PICCS_FWD(FWD_RESID, true); else PICCS_FWD(FWD_RESID, false);
+    } else if (mode == FWD_RESID16) {
+        if (partials) PICCS_FWD(FWD_RESID16, true); else PICCS_FWD(FWD_RESID16, false);
     } else {
         if (partials) PICCS_FWD(FWD_PLAIN, true); else PICCS_FWD(FWD_PLAIN, false);
     }
@@ -353,18 +371,46 @@ cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const 
 
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st, Slots sl)
+                           float *vol, cudaStream_t st, Slots sl, bool rs_bf16)
 {
     const int nb = project_blocks(g);
     if (nb <= 0 || sl.n <= 0) return cudaSuccess;
-    scale_rays_kernel<<<dim3((unsigned)nb, (unsigned)sl.n), 256, 0, st>>>(g, cols, vr, proj, rs,
-                                                                          sl.stride);
     const int per_cta = kGatherThreads * kLayersPerThread;  // layer pairs per CTA
     const int nlp = (g.nz + 1) >> 1;
     const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((nlp + per_cta - 1) / per_cta),
                     (unsigned)sl.n);
-    adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol,
-                                                       sl.stride);
+    const dim3 sgrid((unsigned)nb, (unsigned)sl.n);
+    if (rs_bf16) {
+        __nv_bfloat16 *r16 = reinterpret_cast<__nv_bfloat16 *>(rs);
+        scale_rays_kernel<__nv_bfloat16><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, r16, sl.stride);
+        adj_gather_kernel<__nv_bfloat16><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits,
+                                                                         r16, vol, sl.stride);
+    } else {
+        scale_rays_kernel<float><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, rs, sl.stride);
+        adj_gather_kernel<float><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs,
+                                                                 vol, sl.stride);
+    }
+    return cudaGetLastError();
+}
+
+// Slots' FP32 projections (src_stride bytes apart) rounded to BF16 (to nearest
+// even) into dst (dst_stride bytes apart).
+__global__ void __launch_bounds__(256)
+to_bf16_kernel(long long n, const float *__restrict__ src, long long src_stride,
+               __nv_bfloat16 *__restrict__ dst, long long dst_stride)
+{
+    src = slot_ptr(src, blockIdx.y * src_stride);
+    dst = slot_ptr(dst, blockIdx.y * dst_stride);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+cudaError_t launch_to_bf16(long long n, const float *src, long long src_stride, void *dst,
+                           long long dst_stride, int nslot, cudaStream_t st)
+{
+    to_bf16_kernel<<<dim3(152 * 8, nslot), 256, 0, st>>>(
+        n, src, src_stride, reinterpret_cast<__nv_bfloat16 *>(dst), dst_stride);
     return cudaGetLastError();
 }
 

@@ -53,10 +53,10 @@ struct piccs_ctx {
     LsqrScalars *ls = nullptr;
     // LSQR re-orthogonalisation basis, allocated on first use: per slot the
     // vectors, then the Gram-Schmidt partial sums, basis_bytes apart
-    float *basis = nullptr;
-    int basis_cap = 0;  // vectors
+    void *basis = nullptr;  // FP32 or BF16 vectors, by the run's storage
     double *part_dots = nullptr;
     size_t basis_stride = 0;
+    std::vector<char> staged16;  // slot's staged projections are BF16
     int *flag = nullptr;
     double *dsum = nullptr;
 
@@ -186,6 +186,7 @@ int check_params(const piccs_params *p, char *why, size_t n)
     if (p->x0_mode < 0 || p->x0_mode > 2) { snprintf(why, n, "unknown x0_mode %d", p->x0_mode); return PICCS_EINVAL; }
     if (p->solver < 0 || p->solver > 2) { snprintf(why, n, "unknown solver %d", p->solver); return PICCS_EINVAL; }
     if (p->solver == PICCS_SOLVER_LSQR_REORTH && p->n_inner - 1 > kMaxBasis) { snprintf(why, n, "LSQR_REORTH needs n_inner - 1 <= %d", kMaxBasis); return PICCS_EINVAL; }
+    if (p->storage != PICCS_STORAGE_F32 && p->storage != PICCS_STORAGE_BF16) { snprintf(why, n, "unknown storage %d", p->storage); return PICCS_EINVAL; }
     return PICCS_OK;
 }
 
@@ -252,17 +253,19 @@ T *slot_at(T *p, const piccs_ctx *ctx, int s)
 // cycle needs none) and the Gram-Schmidt partial sums
 size_t basis_vectors(int n_inner) { return n_inner > 1 ? (size_t)(n_inner - 1) : 0; }
 
-size_t basis_vec_bytes(const piccs_geometry *g, int n_inner)
+size_t basis_vec_bytes(const piccs_geometry *g, int n_inner, int storage)
 {
     const size_t M = (size_t)g->nx * g->ny * g->nz;
     const size_t nv = basis_vectors(n_inner) > 0 ? basis_vectors(n_inner) : 1;
-    return align256(nv * (size_t)lsqr_basis_stride((long long)M) * sizeof(float));
+    const size_t es = storage == PICCS_STORAGE_BF16 ? 2 : sizeof(float);
+    return align256(nv * (size_t)lsqr_basis_stride((long long)M) * es);
 }
 
-// per slot: the vectors, then the Gram-Schmidt partial sums
-size_t basis_bytes(const piccs_geometry *g, int n_inner)
+// per slot: the vectors (FP32 or BF16), then the Gram-Schmidt partial sums
+size_t basis_bytes(const piccs_geometry *g, int n_inner, int storage)
 {
-    return basis_vec_bytes(g, n_inner) + align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
+    return basis_vec_bytes(g, n_inner, storage) +
+           align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
 }
 
 }  // namespace
@@ -295,7 +298,7 @@ int piccs_query_workspace_batched(const piccs_geometry *geometry, const piccs_pa
     if (batch < 1 || batch > kMaxSlots) return set_err(nullptr, PICCS_EINVAL, "batch must be in [1, %d]", kMaxSlots);
     *bytes = plan(geometry, batch).total;
     if (params && params->solver == PICCS_SOLVER_LSQR_REORTH)
-        *bytes += (size_t)batch * basis_bytes(geometry, params->n_inner);
+        *bytes += (size_t)batch * basis_bytes(geometry, params->n_inner, params->storage);
     return PICCS_OK;
 }
 
@@ -365,6 +368,7 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
     ctx->hits = reinterpret_cast<CellHit *>(b + L.off_hits);
     ctx->nslot = batch;
     ctx->nactive = batch;
+    ctx->staged16.assign(batch, 0);
     ctx->slot_bytes = L.slot_bytes;
     b += L.off_slot0;  // slot 0; slot s is s * slot_bytes further
     float **img[9] = {&ctx->xprior, &ctx->x, &ctx->p, &ctx->s, &ctx->g,
@@ -574,11 +578,11 @@ int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *p
 
 // One IRN-PICCS reconstruction from device-resident data d_b into ctx->x.
 // Allocates the LSQR re-orthogonalisation basis on first use (synchronises).
-static int ensure_basis(piccs_ctx *ctx, int n_inner)
+static int ensure_basis(piccs_ctx *ctx, int n_inner, int storage)
 {
-    const int need = (int)basis_vectors(n_inner);
-    if (ctx->basis && need <= ctx->basis_cap) return PICCS_OK;
-    const size_t per_slot = basis_bytes(&ctx->geo, n_inner);
+    const size_t per_slot = basis_bytes(&ctx->geo, n_inner, storage);
+    const size_t vec_bytes = basis_vec_bytes(&ctx->geo, n_inner, storage);
+    if (ctx->basis && ctx->basis_stride == per_slot) return PICCS_OK;
     const size_t bytes = per_slot * ctx->nslot;
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
@@ -589,16 +593,15 @@ static int ensure_basis(piccs_ctx *ctx, int n_inner)
     cudaFree(ctx->basis);
     ctx->basis = nullptr;
     ctx->part_dots = nullptr;
-    ctx->basis_cap = 0;
+    ctx->basis_stride = 0;
     void *mem = nullptr;
     if (cudaMalloc(&mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_err(ctx, PICCS_ENOMEM, "cudaMalloc of the LSQR basis (%zu bytes) failed", bytes);
     }
-    ctx->basis = static_cast<float *>(mem);
-    ctx->part_dots = reinterpret_cast<double *>(static_cast<char *>(mem) + basis_vec_bytes(&ctx->geo, n_inner));
+    ctx->basis = mem;
+    ctx->part_dots = reinterpret_cast<double *>(static_cast<char *>(mem) + vec_bytes);
     ctx->basis_stride = per_slot;
-    ctx->basis_cap = need;
     return PICCS_OK;
 }
 
@@ -613,6 +616,7 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     const long long M = ctx->M;
     const float l2p = lam2_piple(p);
     const bool reorth = p->solver == PICCS_SOLVER_LSQR_REORTH;
+    const bool bf16 = p->storage == PICCS_STORAGE_BF16;
     const bool prior_rhs = p->variant == PICCS_VARIANT_PICCS || p->variant == PICCS_VARIANT_PIPLE;
     LsqrScalars *ls = ctx->ls;
     float *z[2] = {ctx->t, ctx->w2sq};
@@ -620,7 +624,8 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     // beta_1 u_1 = b~ - A~ x: uA = b - A x, z = -x, sigma = 1
     if (cycle == 0)
         LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->q,
-                                                         FWD_RESID, d_b, nullptr, &ctx->ks->nonfinite, st, SL(ctx)));
+                                                         bf16 ? FWD_RESID16 : FWD_RESID, d_b, nullptr,
+                                                         &ctx->ks->nonfinite, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ls,
                                                        ctx->part_vec, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st, SL(ctx)));
@@ -631,7 +636,7 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
                                                                ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
     // alpha_1 v_1 = A~^T u_1
     LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
-                                                     ctx->rs, ctx->s, st, SL(ctx)));
+                                                     ctx->rs, ctx->s, st, SL(ctx), bf16));
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr, ls,
                                                     ctx->part_vec, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
@@ -648,21 +653,23 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
         // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
         if (!last)
             LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
-                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
+                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
         const long long ldb = lsqr_basis_stride(M);
-        float *bv = (reorth && !last) ? ctx->basis + (size_t)(i - 1) * ldb : nullptr;
+        void *bv = (reorth && !last)
+                       ? static_cast<char *>(ctx->basis) + (size_t)(i - 1) * ldb * (bf16 ? 2 : sizeof(float))
+                       : nullptr;
         const long long bst = (long long)ctx->basis_stride;
         LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 0, last, ctx->x, ctx->g, ctx->p, ctx->s, bv, ls,
-                                                        ctx->part_vec, st, SL(ctx), bst));
+                                                        ctx->part_vec, st, SL(ctx), bst, bf16));
         if (last) break;
         if (reorth) {
             for (int pass = 0; pass < 2; ++pass) {
                 LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ls, ctx->part_dots, st,
-                                                                  SL(ctx), bst));
+                                                                  SL(ctx), bst, bf16));
                 LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ls, ctx->part_dots, st, SL(ctx), bst));
                 LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_sub(M, ldb, i, ctx->basis, ctx->p, ls,
                                                                  pass == 1 ? ctx->part_vec : nullptr, st, SL(ctx),
-                                                                 bst));
+                                                                 bst, bf16));
             }
         }
         LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 0, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
@@ -670,12 +677,14 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     return PICCS_OK;
 }
 
-// d_b: the slots' projections, slot_bytes apart (any pointer for one slot);
-// d_x0: the slots' initial volumes, x0_pitch bytes apart.
+// d_b: the slots' projections, slot_bytes apart (any pointer for one slot),
+// FP32, or BF16 when p->storage is BF16; d_x0: the slots' initial volumes,
+// x0_pitch bytes apart.
 static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
                                const float *d_x0, size_t x0_pitch)
 {
     cudaStream_t st = ctx->stream;
+    const bool bf16 = p->storage == PICCS_STORAGE_BF16;
     const long long M = ctx->M, N = ctx->N;
     const float l2p = lam2_piple(p);
     const size_t vb = M * sizeof(float), S = ctx->slot_bytes;
@@ -690,11 +699,14 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
     }
     if (p->solver != PICCS_SOLVER_CGLS) {
         if (p->solver == PICCS_SOLVER_LSQR_REORTH) {
-            int rc = ensure_basis(ctx, p->n_inner);
+            int rc = ensure_basis(ctx, p->n_inner, p->storage);
             if (rc != PICCS_OK) return rc;
         }
         if (p->n_inner == 0) {  // no inner step: x stays x0; still flag NaN/Inf in b
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
+            if (bf16)
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite16(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
+            else
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
             return PICCS_OK;
         }
         for (int k = 0; k < p->n_outer; ++k) {
@@ -705,7 +717,8 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         return PICCS_OK;
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r, FWD_RESID, d_b,
+    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r,
+                                 bf16 ? FWD_RESID16 : FWD_RESID, d_b,
                                  nullptr, &ctx->ks->nonfinite, st, SL(ctx)));
     for (int k = 0; k < p->n_outer; ++k) {
         // reweighting at the previous iterate (Eqs. 10-11)
@@ -715,7 +728,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         if (k == 0) {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
                                              ctx->s, 1, nullptr, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st, SL(ctx)));
         } else {
@@ -735,7 +748,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
             // after the reconstruction's last step s = A^T r + g only feeds the
             // history, so its backprojection is skipped
             if (k == p->n_outer - 1 && it == p->n_inner - 1) break;
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st, SL(ctx)));
         }
@@ -763,7 +776,11 @@ int piccs_reconstruct(piccs_ctx *ctx, const float *d_proj, const piccs_params *p
     ctx->nactive = ctx->nslot;
     const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float);
     const float *d_b = d_proj;
-    if (ctx->nslot > 1) {  // the kernels read each slot's projections at its workspace stride
+    if (params->storage == PICCS_STORAGE_BF16) {  // the slots' projections, rounded once
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_to_bf16(ctx->N, d_proj, (long long)pb, ctx->bstage,
+                                                        (long long)ctx->slot_bytes, ctx->nslot, ctx->stream));
+        d_b = ctx->bstage;
+    } else if (ctx->nslot > 1) {  // the kernels read each slot's projections at its workspace stride
         CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, ctx->slot_bytes, d_proj, pb, pb, ctx->nslot,
                                         cudaMemcpyDeviceToDevice, ctx->stream));
         d_b = ctx->bstage;
@@ -803,7 +820,13 @@ int piccs_reconstruct_host(piccs_ctx *ctx, const float *h_proj, const piccs_para
     ctx->nactive = ctx->nslot;
     cudaStream_t st = ctx->stream;
     const size_t vb = ctx->M * sizeof(float), pb = ctx->N * sizeof(float), S = ctx->slot_bytes;
-    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, S, h_proj, pb, pb, ctx->nslot, cudaMemcpyHostToDevice, st));
+    if (params->storage == PICCS_STORAGE_BF16) {  // through the ray scratch, rounded once
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->rs, S, h_proj, pb, pb, ctx->nslot, cudaMemcpyHostToDevice, st));
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_to_bf16(ctx->N, ctx->rs, (long long)S, ctx->bstage,
+                                                        (long long)S, ctx->nslot, st));
+    } else {
+        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->bstage, S, h_proj, pb, pb, ctx->nslot, cudaMemcpyHostToDevice, st));
+    }
     const float *dx0 = nullptr;
     if (params->x0_mode == PICCS_X0_USER) {
         // the initial guesses go through the p buffers, which are free until the first step
@@ -852,6 +875,17 @@ int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host)
     if (slot < 0 || slot >= ctx->nslot || !proj) return set_err(ctx, PICCS_EINVAL, "bad slot or NULL buffer");
     CUDA_TRY(ctx, cudaMemcpyAsync(slot_at(ctx->bstage, ctx, slot), proj, ctx->N * sizeof(float),
                                   from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->staged16[slot] = 0;
+    return PICCS_OK;
+}
+
+int piccs_stage_bf16(piccs_ctx *ctx, int slot, const void *proj, int from_host)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    if (slot < 0 || slot >= ctx->nslot || !proj) return set_err(ctx, PICCS_EINVAL, "bad slot or NULL buffer");
+    CUDA_TRY(ctx, cudaMemcpyAsync(slot_at(ctx->bstage, ctx, slot), proj, ctx->N * 2,
+                                  from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->staged16[slot] = 1;
     return PICCS_OK;
 }
 
@@ -873,8 +907,20 @@ int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, in
     if (params->x0_mode == PICCS_X0_USER) return set_err(ctx, PICCS_EINVAL, "staged runs start from the prior or zero");
     if (needs_prior(params) && !ctx->has_prior) return set_err(ctx, PICCS_EINVAL, "prior not set");
     ctx->nactive = nactive;
+    const bool bf16 = params->storage == PICCS_STORAGE_BF16;
+    for (int b = 0; b < nactive; ++b) {
+        if (ctx->staged16[b] && !bf16)
+            return set_err(ctx, PICCS_EINVAL, "slot %d holds BF16 projections; the run needs storage BF16", b);
+        if (bf16 && !ctx->staged16[b]) {  // round the staged FP32 projections, through the ray scratch
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_to_bf16(ctx->N, slot_at(ctx->bstage, ctx, b), 0,
+                                                            slot_at(ctx->rs, ctx, b), 0, 1, ctx->stream));
+            CUDA_TRY(ctx, cudaMemcpyAsync(slot_at(ctx->bstage, ctx, b), slot_at(ctx->rs, ctx, b), ctx->N * 2,
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+            ctx->staged16[b] = 1;
+        }
+    }
     if (params->solver == PICCS_SOLVER_LSQR_REORTH) {  // allocate before any capture
-        int rc = ensure_basis(ctx, params->n_inner);
+        int rc = ensure_basis(ctx, params->n_inner, params->storage);
         if (rc != PICCS_OK) return rc;
     }
     if (!use_graph || ctx->timing) return enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);

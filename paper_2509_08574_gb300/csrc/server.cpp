@@ -36,7 +36,7 @@ double ms_between(Clock::time_point a, Clock::time_point b)
 struct Request {
     long long id = 0;
     int patient = 0;
-    const float *h_proj = nullptr;
+    const void *h_proj = nullptr;  // FP32, or BF16 for PICCS_STORAGE_BF16 requests
     float *h_out = nullptr;
     piccs_params params{};
     Clock::time_point t_submit, t_issue, t_done;
@@ -250,7 +250,10 @@ bool issue_batch(piccs_server *srv, Session &s)
     for (int i = 0; i < n; ++i) {
         batch[i]->t_issue = now;
         batch[i]->batch = n;
-        if (rc == PICCS_OK) rc = piccs_stage(s.ctx, i, batch[i]->h_proj, 1);
+        if (rc == PICCS_OK)
+            rc = head->params.storage == PICCS_STORAGE_BF16
+                     ? piccs_stage_bf16(s.ctx, i, batch[i]->h_proj, 1)
+                     : piccs_stage(s.ctx, i, static_cast<const float *>(batch[i]->h_proj), 1);
     }
     if (rc == PICCS_OK) rc = piccs_run_staged(s.ctx, n, &head->params, srv->cfg.use_graphs);
     for (int i = 0; i < n && rc == PICCS_OK; ++i) rc = piccs_unstage(s.ctx, i, batch[i]->h_out, 1);
@@ -458,7 +461,7 @@ int piccs_server_add_patient(piccs_server *srv, int patient, const piccs_geometr
     return PICCS_OK;
 }
 
-int piccs_server_submit(piccs_server *srv, int patient, const float *h_proj,
+int piccs_server_submit(piccs_server *srv, int patient, const void *h_proj,
                         const piccs_params *params, float *h_out, long long *ticket)
 {
     if (!srv || !h_proj || !params || !h_out || !ticket) return fail(srv, PICCS_EINVAL, "NULL argument");

@@ -468,3 +468,17 @@ def random_volume(g: Geometry, seed: int, smooth: bool = False) -> np.ndarray:
 def random_projections(g: Geometry, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(0.0, 1.0, size=g.proj_shape())
+
+
+def bf16_bits(x) -> np.ndarray:
+    """Round float32 values to bfloat16 (to nearest, ties to even) and return
+    the 16-bit patterns (uint16): keep the upper half of the float32 bits after
+    adding 0x7FFF plus the lowest kept bit.  Finite inputs only."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = u + 0x7FFF + ((u >> 16) & 1)
+    return (u >> 16).astype(np.uint16)
+
+
+def bf16_values(bits) -> np.ndarray:
+    """float32 values of bfloat16 bit patterns."""
+    return (np.asarray(bits, dtype=np.uint32) << 16).view(np.float32)

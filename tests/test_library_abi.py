@@ -112,3 +112,24 @@ def test_batched_workspace(pk):
     for bad in (0, -1, 65):
         with pytest.raises(pk.PiccsError):
             pk.piccs_query_workspace_batched(g, None, bad)
+
+
+def test_bf16_rounding_helper_matches_torch():
+    """The host BF16 rounding used to make BF16 test inputs is round to
+    nearest even, as torch's float32 -> bfloat16 conversion."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.integers(-6, 6, size=4000),
+                        [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -0.0, 65504.0, 3e38]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    np.testing.assert_array_equal(P.bf16_bits(x), ref)
+    np.testing.assert_array_equal(P.bf16_values(ref), torch.from_numpy(x).to(torch.bfloat16).float().numpy())
+
+
+def test_storage_parameter(pk):
+    g = P.c2_needle().geometry
+    f32 = pk.piccs_query_workspace(g, pk.make_params(solver=2, n_inner=10))
+    b16 = pk.piccs_query_workspace(g, pk.make_params(solver=2, n_inner=10, storage=pk.STORAGE_BF16))
+    assert f32 - b16 >= 9 * 2 * g.M  # the basis is half the size
+    with pytest.raises(pk.PiccsError):
+        pk.piccs_validate(g, pk.make_params(storage=2))
