@@ -49,6 +49,8 @@ def parse_args():
                     help="inner Krylov solver (LSQR and CGLS are equivalent in exact arithmetic)")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="c2_needle",
                     help="c2_needle: the 256^3 scan the headline is quoted on; c1_small: 64^3")
+    ap.add_argument("--storage", choices=["f32", "bf16"], default="f32",
+                    help="bf16: projections, backprojected ray values and the LSQR basis in BF16")
     ap.add_argument("--batch", type=int, default=1,
                     help="scans reconstructed together per step (one launch per kernel for all)")
     ap.add_argument("--serving", action="store_true",
@@ -311,8 +313,9 @@ def run_ours(args):
         xp = xp.unsqueeze(0).expand((B,) + tuple(xp.shape)).contiguous()
     out = torch.empty(((B,) if B > 1 else ()) + g.vol_shape(), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    storage = pk.STORAGE_BF16 if args.storage == "bf16" else pk.STORAGE_F32
     params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner,
-                            solver=SOLVERS[args.solver][0])
+                            solver=SOLVERS[args.solver][0], storage=storage)
     torch.cuda.synchronize()
     ctx = pk.Context(g, stream=stream, batch=B)
     ctx.set_prior(xp)
@@ -390,7 +393,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(scan, args.solver,
                                        pk.piccs_query_workspace_batched(g, params, B)),
-                       batch=B),
+                       batch=B, storage=args.storage),
         "p50_ms": p50, "p99_ms": p99,
         "job_scans_per_s": world * args.steps * B / (total_ms * B * 1e-3),
         "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(B * g.N * 4),
@@ -409,6 +412,20 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed_region": t_wall, "input_generation_s": t_in,
     }
+    if storage == pk.STORAGE_BF16 and rank == 0:
+        # image error of the BF16 path: against the FP32 path and the ground truth
+        with torch.cuda.stream(stream):
+            xb = ctx.reconstruct(b, params, out=out).clone()
+            p32 = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner,
+                                 solver=SOLVERS[args.solver][0])
+            x32 = ctx.reconstruct(b, p32, out=out).clone()
+        stream.synchronize()
+        xb, x32 = xb.reshape(-1, g.M)[0].double(), x32.reshape(-1, g.M)[0].double()
+        truth = torch.from_numpy(scan.truth_volume(ss=1).reshape(-1)).double().cuda()
+        rel = lambda a, c: float(torch.linalg.norm(a - c) / torch.linalg.norm(c))
+        line["error"] = {"rel_l2_bf16_vs_f32": rel(xb, x32),
+                         "rel_l2_to_truth": {"f32": rel(x32, truth), "bf16": rel(xb, truth)}}
+        line["dtype"] = "bf16 storage, f32 accumulation, f64 scalars"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_sample(scan, b_np, xp_np)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -512,6 +529,7 @@ def run_serving(args):
         counts = torch.poisson(5e4 * torch.exp(-li), generator=gen)
         b = -torch.log(torch.clamp(counts, min=1.0) / 5e4)
         data.append(dict(prior=xp.cpu().numpy(), proj=b.cpu().pin_memory(),
+                         proj16=b.to(torch.bfloat16).cpu().pin_memory(),
                          params=pk.make_params(0.5, 0.5, 1e-2, p["n_outer"], p["n_inner"],
                                                solver=SOLVERS[args.solver][0])))
         del xp, xt, li, counts, b
@@ -548,42 +566,54 @@ def run_serving(args):
         c.close()
     torch.cuda.synchronize()
 
-    # served: the request loop
-    outs = outbufs()
-    srv = pk.Server(max_batch=8, max_running=2, use_graphs=True)
-    for k, (p, d) in enumerate(zip(pats, data)):
-        srv.add_patient(k, p["geometry"], d["prior"])
-    for k in range(len(pats)):  # warm: sessions resident, graphs captured for batch 1
-        t, _ = srv.submit(k, data[k]["proj"], data[k]["params"], out=outs[k][0])
-        srv.wait(t)
-    warm = srv.stats()
-    tickets = [None] * args.requests
-    t0 = time.perf_counter()
-
-    def feeder():
-        for r in range(args.requests):
-            now = time.perf_counter() - t0
-            if now < arrivals[r]:
-                time.sleep(arrivals[r] - now)
-            k = int(who[r])
-            tickets[r] = srv.submit(k, data[k]["proj"], data[k]["params"], out=outs[k][r % 2])[0]
-
-    th = threading.Thread(target=feeder)
-    th.start()
-    th.join()
-    st = [srv.wait(t) for t in tickets]
-    span_served = time.perf_counter() - t0
-    sstats = srv.stats()
-    srv.close()
-    if any(x["status"] != 0 for x in st):
-        raise RuntimeError("served request failed")
-    lat_served = [x["total_ms"] for x in st]
-
     def summary(lat, span):
         return {"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99),
                 "scans_per_s": args.requests / span, "makespan_s": span}
 
-    served, plain = summary(lat_served, span_served), summary(lat_plain, span_plain)
+    # served: the request loop (FP32 storage, then BF16 storage with BF16 inputs)
+    def served_arm(bf16):
+        outs = outbufs()
+        srv = pk.Server(max_batch=8, max_running=2, use_graphs=True)
+        prm = []
+        for k, (p, d) in enumerate(zip(pats, data)):
+            srv.add_patient(k, p["geometry"], d["prior"])
+            q = d["params"]
+            prm.append(pk.make_params(q.alpha, q.lambda_, q.tau, q.n_outer, q.n_inner,
+                                      solver=q.solver,
+                                      storage=pk.STORAGE_BF16 if bf16 else pk.STORAGE_F32))
+        src = "proj16" if bf16 else "proj"
+        for k in range(len(pats)):  # warm: sessions resident, graphs captured for batch 1
+            t, _ = srv.submit(k, data[k][src], prm[k], out=outs[k][0])
+            srv.wait(t)
+        warm = srv.stats()
+        tickets = [None] * args.requests
+        t0 = time.perf_counter()
+
+        def feeder():
+            for r in range(args.requests):
+                now = time.perf_counter() - t0
+                if now < arrivals[r]:
+                    time.sleep(arrivals[r] - now)
+                k = int(who[r])
+                tickets[r] = srv.submit(k, data[k][src], prm[k], out=outs[k][r % 2])[0]
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        st = [srv.wait(t) for t in tickets]
+        span = time.perf_counter() - t0
+        sstats = srv.stats()
+        srv.close()
+        if any(x["status"] != 0 for x in st):
+            raise RuntimeError("served request failed")
+        res = summary([x["total_ms"] for x in st], span)
+        res.update(max_batch=8, max_running=2, graphs=True, storage="bf16" if bf16 else "f32",
+                   mean_batch=args.requests / max(sstats["batches"] - warm["batches"], 1),
+                   server=sstats)
+        return res
+
+    served, served16 = served_arm(False), served_arm(True)
+    plain = summary(lat_plain, span_plain)
     line = {
         "metric": "serving latency p50/p99 and scans/s (Poisson request stream, 16 patients)",
         "value": served["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
@@ -594,9 +624,8 @@ def run_serving(args):
                    "solver": args.solver,
                    "patients": [[p["geometry"].nx, p["geometry"].n_views, p["geometry"].nu,
                                  p["n_outer"] * p["n_inner"]] for p in pats]},
-        "served": dict(served, max_batch=8, max_running=2, graphs=True,
-                       mean_batch=args.requests / max(sstats["batches"] - warm["batches"], 1),
-                       server=sstats),
+        "served": served,
+        "served_bf16": served16,
         "plain_one_at_a_time": plain,
         "input_generation_s": t_in,
     }
