@@ -253,7 +253,7 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // exact piece length -- the expression the forward walk evaluates -- which is
 // also the length of row nv-1-r in layer p.
 template <class RT>
-__global__ void __launch_bounds__(kGatherThreads)
+__global__ void __launch_bounds__(kGatherThreads, 32)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
                   const RT *__restrict__ rs, float *__restrict__ vol, long long sstride)

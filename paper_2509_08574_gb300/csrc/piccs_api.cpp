@@ -64,6 +64,7 @@ struct piccs_ctx {
     struct GraphEntry { cudaGraphExec_t exec = nullptr; long long launches[PICCS_KERNEL_CLASSES] = {}; };
     std::map<std::string, GraphEntry> graphs;
     long long graph_launches = 0;
+    cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot capture)
     // kernel accounting
     bool timing = false;
     long long launches[PICCS_KERNEL_CLASSES] = {};
@@ -428,6 +429,7 @@ void piccs_destroy(piccs_ctx *ctx)
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->basis);
     cudaFree(ctx->base);
     delete ctx;
@@ -932,10 +934,17 @@ int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, in
     if (it == ctx->graphs.end()) {
         long long before[PICCS_KERNEL_CLASSES];
         std::memcpy(before, ctx->launches, sizeof before);
-        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        if (!ctx->cap_stream)
+            CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        // capture on the private stream (nothing runs during a capture), then
+        // launch the graph on the context's stream
+        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t user = ctx->stream;
+        ctx->stream = ctx->cap_stream;
         int rc = enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);
+        ctx->stream = user;
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (rc != PICCS_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             return rc != PICCS_OK ? rc : set_err(ctx, PICCS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
