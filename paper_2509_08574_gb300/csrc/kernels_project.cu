@@ -41,9 +41,21 @@ namespace piccs {
 
 namespace {
 
+// Gather shape: threads per CTA, layer pairs per thread, and the CTAs per SM
+// the register allocation must allow (compile-time, for tuning sweeps).
+#ifndef PICCS_GATHER_THREADS
+#define PICCS_GATHER_THREADS 64
+#endif
+#ifndef PICCS_GATHER_LAYERS
+#define PICCS_GATHER_LAYERS 2
+#endif
+#ifndef PICCS_GATHER_MIN_CTAS
+#define PICCS_GATHER_MIN_CTAS 32
+#endif
+
 constexpr int kRowGroups = 8;    // warps per forward CTA: 8 x 32 row pairs of one column
-constexpr int kGatherThreads = 64;
-constexpr int kLayersPerThread = 2;  // layer pairs per gather thread
+constexpr int kGatherThreads = PICCS_GATHER_THREADS;
+constexpr int kLayersPerThread = PICCS_GATHER_LAYERS;  // layer pairs per gather thread
 constexpr unsigned kFull = 0xffffffffu;
 
 // per-ray factor: 3D length per unit of xy length
@@ -253,7 +265,7 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // exact piece length -- the expression the forward walk evaluates -- which is
 // also the length of row nv-1-r in layer p.
 template <class RT>
-__global__ void __launch_bounds__(kGatherThreads, 32)
+__global__ void __launch_bounds__(kGatherThreads, PICCS_GATHER_MIN_CTAS)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
                   const RT *__restrict__ rs, float *__restrict__ vol, long long sstride)
