@@ -14,7 +14,7 @@ import oracle as O  # noqa: E402
 import phantoms as P  # noqa: E402
 
 out = {}
-for make in (P.c1_small, P.c2_needle):
+for make in (P.c1_small, P.c2_needle, P.c3_sphere_growth, P.c5_carm):
     scan = make()
     g = scan.geometry
     out[scan.name] = {"nnz": O.count_nnz(g), "M": g.M, "N": g.N}
