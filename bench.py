@@ -400,7 +400,9 @@ def run_ours(args):
     kernel_names = {"forward": "fwd_kernel", "adjoint": "scale_rays_kernel+adj_gather_kernel"}
 
     line = {
-        "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "c2_needle" else
+                  f"PICCS-Krylov recon ms/scan p50, {scan.name} ({scan.iterations} its)",
+        "value": p50, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms * B / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(scan, args.solver,
