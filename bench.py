@@ -456,8 +456,10 @@ def run_ours(args):
 
 
 def run_kernels_only(args):
-    """A (forward) and A^T (adjoint) launches on the 256^3 workload, each
-    preceded by an L2 flush; prints their CUDA-event times."""
+    """The hot kernels alone on the workload, each launch preceded by an L2
+    flush: A (forward), A^T (adjoint), the regularisation normal operator
+    D^T Omega D z with its energy (reg_normal) and the IRN reweighting
+    (weights + prior right-hand side); prints their CUDA-event times."""
     import torch
     import paper_2509_08574_gb300 as pk
 
@@ -468,18 +470,27 @@ def run_kernels_only(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     q = torch.empty(g.proj_shape(), dtype=torch.float32, device="cuda")
     s = torch.empty(g.vol_shape(), dtype=torch.float32, device="cuda")
+    params = pk.make_params(scan.alpha, scan.lam, scan.tau, 1, 1)
     stream = torch.cuda.current_stream()
     with pk.Context(g, stream=stream) as ctx:
-        times = {"forward": [], "adjoint": []}
+        ctx.set_prior(x)
+        z = 1.01 * x
+        omega, c = ctx.reg_weights(z, params)
+        t = torch.empty_like(z)
+        times = {"forward": [], "adjoint": [], "reg_normal": [], "reweight": []}
         for _ in range(max(args.steps, 1)):
-            for kind in ("forward", "adjoint"):
+            for kind in times:
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 if kind == "forward":
                     ctx.forward(x, q)
-                else:
+                elif kind == "adjoint":
                     ctx.adjoint(y, s)
+                elif kind == "reg_normal":
+                    pk.piccs_reg_normal(ctx.h, omega, params, z, t, False)
+                else:
+                    ctx.reg_weights(z, params, omega, c)
                 e1.record()
                 torch.cuda.synchronize()
                 times[kind].append(e0.elapsed_time(e1))
