@@ -28,26 +28,34 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Visits every voxel once.  The threads of a block form groups of nzr (nz
-// rounded up to whole warps, at most the block), one xy column (ix * ny + iy)
-// per group; the block's groups take consecutive columns and the grid strides
-// over them, stepping (ix, iy) without division.  f(i, ix, iy, iz), i the flat
-// index.
+// Visits every voxel once.  The threads of a block form groups of nzr (half
+// of nz, rounded up to whole warps, at most the block), one xy column
+// (ix * ny + iy) per group, each thread two z layers nzr apart so that two
+// voxels' loads are in flight; the block's groups take consecutive columns
+// and the grid strides over them, stepping (ix, iy) without division.
+// f(i, ix, iy, iz), i the flat index (32-bit: the volume has < 2^31 voxels).
 template <class F>
 __device__ __forceinline__ void for_voxels(const VolDims &d, F &&f)
 {
-    const int nzr = min((d.nz + 31) / 32 * 32, (int)blockDim.x);
+    constexpr int kPer = 2;  // voxels per thread and column
+    const int nzr = min(((d.nz + kPer - 1) / kPer + 31) / 32 * 32, (int)blockDim.x);
     const int cpi = (int)blockDim.x / nzr;
     const int sub = (int)threadIdx.x / nzr, tz = (int)threadIdx.x - sub * nzr;
     if (sub >= cpi) return;
-    const int ncol = d.nx * d.ny;  // < 2^31 (the volume is)
+    const int ncol = d.nx * d.ny;
     const int step = (int)gridDim.x * cpi;
     const int step_x = step / d.ny, step_y = step - step_x * d.ny;
     int col = (int)blockIdx.x * cpi + sub;
     int ix = col / d.ny, iy = col - ix * d.ny;
     for (; col < ncol; col += step) {
-        const long long base = (long long)col * d.nz;
-        for (int iz = tz; iz < d.nz; iz += nzr) f(base + iz, ix, iy, iz);
+        const int base = col * d.nz;
+        for (int z0 = tz; z0 < d.nz; z0 += kPer * nzr) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int iz = z0 + k * nzr;
+                if (iz < d.nz) f(base + iz, ix, iy, iz);
+            }
+        }
         ix += step_x;
         iy += step_y;
         if (iy >= d.ny) {
@@ -88,9 +96,9 @@ weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float 
     xp = slot_ptr(xp, so);
     omega = slot_ptr(omega, so);
     w2sq = slot_ptr(w2sq, so);
-    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    const int sx = d.ny * d.nz, sy = d.nz;
     (void)M;
-    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
+    for_voxels(d, [&](int i, int ix, int iy, int iz) {
         const float xi = x[i];
         const float gx = (ix + 1 < d.nx) ? xi - x[i + sx] : 0.f;
         const float gy = (iy + 1 < d.ny) ? xi - x[i + sy] : 0.f;
@@ -120,9 +128,9 @@ prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
     xp = slot_ptr(xp, so);
     w2sq = slot_ptr(w2sq, so);
     c = slot_ptr(c, so);
-    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    const int sx = d.ny * d.nz, sy = d.nz;
     (void)M;
-    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
+    for_voxels(d, [&](int i, int ix, int iy, int iz) {
         float out = 0.f;
         if (variant == 0) {
             const float pi = xp[i], wi = w2sq[i];
@@ -142,12 +150,12 @@ prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
 }
 
 // t = D^T diag(omega) D z (+ lam2 z) at voxel i, and omega |(Dz)_i|^2 (+ lam2 z_i^2)
-__device__ __forceinline__ float stencil_at(const VolDims &d, long long i, int ix, int iy, int iz,
+__device__ __forceinline__ float stencil_at(const VolDims &d, int i, int ix, int iy, int iz,
                                             const float *__restrict__ z,
                                             const float *__restrict__ omega, float lam2,
                                             float &energy)
 {
-    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    const int sx = d.ny * d.nz, sy = d.nz;
     const float zi = z[i];
     const float w = omega[i];
     const float gx = (ix + 1 < d.nx) ? zi - z[i + sx] : 0.f;
@@ -190,7 +198,7 @@ reg_normal_kernel(VolDims d, long long M, const float *__restrict__ z,
     partials = slot_ptr(partials, so);
     KahanF acc;
     (void)M;
-    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
+    for_voxels(d, [&](int i, int ix, int iy, int iz) {
         float e;
         out[i] = stencil_at(d, i, ix, iy, iz, z, omega, lam2, e);
         if (NORM) acc.add(e);
@@ -213,7 +221,7 @@ reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
     partials = slot_ptr(partials, so);
     KahanF acc;
     (void)M;
-    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
+    for_voxels(d, [&](int i, int ix, int iy, int iz) {
         float e;
         const float gn = c[i] - stencil_at(d, i, ix, iy, iz, x, omega, lam2, e);
         const float sn = first ? gn : s[i] + (gn - g[i]);
@@ -277,11 +285,11 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
         cb = co[1];
         sig = co[2];
     }
-    auto zn = [&](long long j) { return INIT ? -src[j] : fmaf(ca, src[j], -cb * zold[j]); };
-    const long long sx = (long long)d.ny * d.nz, sy = d.nz;
+    auto zn = [&](int j) { return INIT ? -src[j] : fmaf(ca, src[j], -cb * zold[j]); };
+    const int sx = d.ny * d.nz, sy = d.nz;
     KahanF k0, k1, k2;
     (void)M;
-    for_voxels(d, [&](long long i, int ix, int iy, int iz) {
+    for_voxels(d, [&](int i, int ix, int iy, int iz) {
         const float zi = zn(i);
         const float w = omega[i];
         const float gx = (ix + 1 < d.nx) ? zi - zn(i + sx) : 0.f;
