@@ -160,15 +160,17 @@ cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, fl
                                const float *c, float *g, float *s, int first, double *partials,
                                cudaStream_t st, Slots sl = Slots{1, 0});
 
-// LSQR z-step and the regularisation part of A~^T u (see LsqrScalars):
-// init: z' = -src, sigma' = 1; else z' = co[0] src - co[1] z (co = LsqrScalars::ureg,
-// sigma' = co[2]); then s = K z' + sigma' c.  partials: 2 (init: 3) arrays of
-// stencil_blocks(M) doubles, [z'.K z' | <z', c> | <x_p, c>].  Skipped when
-// co[3] != 0 (not in init).
-cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
-                             float *znew, const float *omega, float lam2_piple, const float *c,
-                             const float *xp, float *s, const float *co, double *partials,
-                             cudaStream_t st, Slots sl = Slots{1, 0});
+// LSQR z-step (see LsqrScalars): init: z' = -src; else z' = co[0] src -
+// co[1] zold (co = LsqrScalars::ureg); skipped when co[3] != 0 (not in init).
+cudaError_t launch_lsqr_zstep(VolDims d, int init, const float *src, const float *zold, float *znew,
+                              const float *co, cudaStream_t st, Slots sl = Slots{1, 0});
+// The regularisation part of A~^T u: s = K z + sigma c (sigma = 1 in init,
+// else co[2]); partials: 2 (init: 3) arrays of stencil_blocks(M) doubles,
+// [z.K z | <z, c> | <x_p, c>].  Skipped when co[3] != 0 (not in init).
+cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *z, const float *omega,
+                             float lam2_piple, const float *c, const float *xp, float *s,
+                             const float *co, double *partials, cudaStream_t st,
+                             Slots sl = Slots{1, 0});
 
 // ---- Krylov vector work (kernels_krylov.cu) ----
 // (Slots: see above; bstride = the per-slot stride of the LSQR basis region,

@@ -28,16 +28,15 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Visits every voxel once.  The threads of a block form groups of nzr (half
-// of nz, rounded up to whole warps, at most the block), one xy column
-// (ix * ny + iy) per group, each thread two z layers nzr apart so that two
-// voxels' loads are in flight; the block's groups take consecutive columns
-// and the grid strides over them, stepping (ix, iy) without division.
+// Visits every voxel once.  The threads of a block form groups of nzr (nz /
+// kPer, rounded up to whole warps, at most the block), one xy column
+// (ix * ny + iy) per group, each thread kPer z layers nzr apart so that
+// several voxels' loads are in flight; the block's groups take consecutive
+// columns and the grid strides over them, stepping (ix, iy) without division.
 // f(i, ix, iy, iz), i the flat index (32-bit: the volume has < 2^31 voxels).
-template <class F>
+template <int kPer, class F>
 __device__ __forceinline__ void for_voxels(const VolDims &d, F &&f)
 {
-    constexpr int kPer = 2;  // voxels per thread and column
     const int nzr = min(((d.nz + kPer - 1) / kPer + 31) / 32 * 32, (int)blockDim.x);
     const int cpi = (int)blockDim.x / nzr;
     const int sub = (int)threadIdx.x / nzr, tz = (int)threadIdx.x - sub * nzr;
@@ -98,7 +97,7 @@ weights_kernel(VolDims d, long long M, const float *__restrict__ x, const float 
     w2sq = slot_ptr(w2sq, so);
     const int sx = d.ny * d.nz, sy = d.nz;
     (void)M;
-    for_voxels(d, [&](int i, int ix, int iy, int iz) {
+    for_voxels<1>(d, [&](int i, int ix, int iy, int iz) {
         const float xi = x[i];
         const float gx = (ix + 1 < d.nx) ? xi - x[i + sx] : 0.f;
         const float gy = (iy + 1 < d.ny) ? xi - x[i + sy] : 0.f;
@@ -130,7 +129,7 @@ prior_rhs_kernel(VolDims d, long long M, const float *__restrict__ xp,
     c = slot_ptr(c, so);
     const int sx = d.ny * d.nz, sy = d.nz;
     (void)M;
-    for_voxels(d, [&](int i, int ix, int iy, int iz) {
+    for_voxels<1>(d, [&](int i, int ix, int iy, int iz) {
         float out = 0.f;
         if (variant == 0) {
             const float pi = xp[i], wi = w2sq[i];
@@ -198,7 +197,7 @@ reg_normal_kernel(VolDims d, long long M, const float *__restrict__ z,
     partials = slot_ptr(partials, so);
     KahanF acc;
     (void)M;
-    for_voxels(d, [&](int i, int ix, int iy, int iz) {
+    for_voxels<2>(d, [&](int i, int ix, int iy, int iz) {
         float e;
         out[i] = stencil_at(d, i, ix, iy, iz, z, omega, lam2, e);
         if (NORM) acc.add(e);
@@ -221,7 +220,7 @@ reg_restart_kernel(VolDims d, long long M, const float *__restrict__ x,
     partials = slot_ptr(partials, so);
     KahanF acc;
     (void)M;
-    for_voxels(d, [&](int i, int ix, int iy, int iz) {
+    for_voxels<2>(d, [&](int i, int ix, int iy, int iz) {
         float e;
         const float gn = c[i] - stencil_at(d, i, ix, iy, iz, x, omega, lam2, e);
         const float sn = first ? gn : s[i] + (gn - g[i]);
@@ -254,23 +253,20 @@ __device__ __forceinline__ void block_sums_store(const double (&v)[NV], double *
     }
 }
 
-// LSQR z-step fused with the regularisation part of A~^T u.  The new z at a
-// voxel is formed where it is needed (z' = ca src - cb zold, or -src in the
-// first step of a cycle), so the 7-point stencil K z' reads src and zold at
-// the neighbours and z' is written to a second buffer.
+// Regularisation part of A~^T u for LSQR: s = K z + sigma c with K the
+// regularisation normal operator, and the partial sums z.K z, <z, c> (and,
+// in the first step of a cycle, <x_p, c> = |b_R|^2); z was formed by
+// lsqr_zstep_kernel.
 template <bool INIT>
 __global__ void __launch_bounds__(kThreads)
-lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
-                 const float *__restrict__ zold, float *__restrict__ znew,
+lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ z,
                  const float *__restrict__ omega, float lam2, const float *__restrict__ c,
                  const float *__restrict__ xp, float *__restrict__ s,
                  const float *__restrict__ co, double *__restrict__ partials, long long sstride)
 {
     {
         const long long so = blockIdx.y * sstride;
-        src = slot_ptr(src, so);
-        zold = slot_ptr(zold, so);
-        znew = slot_ptr(znew, so);
+        z = slot_ptr(z, so);
         omega = slot_ptr(omega, so);
         c = slot_ptr(c, so);
         xp = slot_ptr(xp, so);
@@ -278,33 +274,20 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
         co = slot_ptr(co, so);
         partials = slot_ptr(partials, so);
     }
-    float ca = -1.f, cb = 0.f, sig = 1.f;
+    float sig = 1.f;
     if (!INIT) {
         if (co[3] != 0.f) return;
-        ca = co[0];
-        cb = co[1];
         sig = co[2];
     }
-    auto zn = [&](int j) { return INIT ? -src[j] : fmaf(ca, src[j], -cb * zold[j]); };
-    const int sx = d.ny * d.nz, sy = d.nz;
     KahanF k0, k1, k2;
     (void)M;
-    for_voxels(d, [&](int i, int ix, int iy, int iz) {
-        const float zi = zn(i);
-        const float w = omega[i];
-        const float gx = (ix + 1 < d.nx) ? zi - zn(i + sx) : 0.f;
-        const float gy = (iy + 1 < d.ny) ? zi - zn(i + sy) : 0.f;
-        const float gz = (iz + 1 < d.nz) ? zi - zn(i + 1) : 0.f;
-        float t = w * (gx + gy + gz);
-        if (ix >= 1) t -= omega[i - sx] * (zn(i - sx) - zi);
-        if (iy >= 1) t -= omega[i - sy] * (zn(i - sy) - zi);
-        if (iz >= 1) t -= omega[i - 1] * (zn(i - 1) - zi);
-        t = fmaf(lam2, zi, t);
+    for_voxels<2>(d, [&](int i, int ix, int iy, int iz) {
+        float e;
+        const float t = stencil_at(d, i, ix, iy, iz, z, omega, lam2, e);
         const float ci = c[i];
-        znew[i] = zi;
         s[i] = fmaf(sig, ci, t);
-        k0.add(w * (gx * gx + gy * gy + gz * gz) + lam2 * zi * zi);
-        k1.add(zi * ci);
+        k0.add(e);
+        k1.add(z[i] * ci);
         if (INIT && xp) k2.add(xp[i] * ci);  // |b_R|^2 (no prior: b_R = 0)
     });
     const double acc[3] = {k0.value(), k1.value(), k2.value()};
@@ -314,6 +297,48 @@ lsqr_ureg_kernel(VolDims d, long long M, const float *__restrict__ src,
         const double a2[2] = {acc[0], acc[1]};
         block_sums_store<2>(a2, partials);
     }
+}
+
+// LSQR z-step: z' = co[0] src - co[1] zold (init: z' = -src), four voxels a
+// thread at a time.
+template <bool INIT>
+__global__ void __launch_bounds__(kThreads)
+lsqr_zstep_kernel(long long M, const float *__restrict__ src, const float *__restrict__ zold,
+                  float *__restrict__ znew, const float *__restrict__ co, long long sstride)
+{
+    {
+        const long long so = blockIdx.y * sstride;
+        src = slot_ptr(src, so);
+        zold = slot_ptr(zold, so);
+        znew = slot_ptr(znew, so);
+        co = slot_ptr(co, so);
+    }
+    float ca = -1.f, cb = 0.f;
+    if (!INIT) {
+        if (co[3] != 0.f) return;
+        ca = co[0];
+        cb = co[1];
+    }
+    const long long n4 = M >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    const float4 *o4 = reinterpret_cast<const float4 *>(zold);
+    float4 *n4p = reinterpret_cast<float4 *>(znew);
+    for (long long i = t0; i < n4; i += stride) {
+        const float4 a = s4[i];
+        float4 r;
+        if (INIT) {
+            r = make_float4(-a.x, -a.y, -a.z, -a.w);
+        } else {
+            const float4 b = o4[i];
+            r = make_float4(fmaf(ca, a.x, -cb * b.x), fmaf(ca, a.y, -cb * b.y),
+                            fmaf(ca, a.z, -cb * b.z), fmaf(ca, a.w, -cb * b.w));
+        }
+        n4p[i] = r;
+    }
+    for (long long i = (n4 << 2) + t0; i < M; i += stride)
+        znew[i] = INIT ? -src[i] : fmaf(ca, src[i], -cb * zold[i]);
 }
 
 }  // namespace
@@ -369,19 +394,30 @@ cudaError_t launch_reg_restart(VolDims d, const float *x, const float *omega, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *src, const float *zold,
-                             float *znew, const float *omega, float lam2_piple, const float *c,
-                             const float *xp, float *s, const float *co, double *partials,
-                             cudaStream_t st, Slots sl)
+cudaError_t launch_lsqr_zstep(VolDims d, int init, const float *src, const float *zold, float *znew,
+                              const float *co, cudaStream_t st, Slots sl)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    const dim3 grid(152 * 8, sl.n);
+    if (init)
+        lsqr_zstep_kernel<true><<<grid, kThreads, 0, st>>>(M, src, zold, znew, co, sl.stride);
+    else
+        lsqr_zstep_kernel<false><<<grid, kThreads, 0, st>>>(M, src, zold, znew, co, sl.stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lsqr_ureg(VolDims d, int init, const float *z, const float *omega,
+                             float lam2_piple, const float *c, const float *xp, float *s,
+                             const float *co, double *partials, cudaStream_t st, Slots sl)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
     const dim3 grid(stencil_blocks(M), sl.n);
     if (init)
-        lsqr_ureg_kernel<true><<<grid, kThreads, 0, st>>>(d, M, src, zold, znew, omega, lam2_piple,
-                                                          c, xp, s, co, partials, sl.stride);
+        lsqr_ureg_kernel<true><<<grid, kThreads, 0, st>>>(d, M, z, omega, lam2_piple, c, xp, s, co,
+                                                          partials, sl.stride);
     else
-        lsqr_ureg_kernel<false><<<grid, kThreads, 0, st>>>(d, M, src, zold, znew, omega, lam2_piple,
-                                                           c, xp, s, co, partials, sl.stride);
+        lsqr_ureg_kernel<false><<<grid, kThreads, 0, st>>>(d, M, z, omega, lam2_piple, c, xp, s, co,
+                                                           partials, sl.stride);
     return cudaGetLastError();
 }
 

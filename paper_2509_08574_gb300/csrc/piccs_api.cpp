@@ -631,7 +631,8 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ls,
                                                        ctx->part_vec, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, ctx->x, nullptr, z[cur], ctx->omega, l2p, ctx->c,
+    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 1, ctx->x, nullptr, z[cur], nullptr, st, SL(ctx)));
+    LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, z[cur], ctx->omega, l2p, ctx->c,
                                                    prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
                                                    ctx->part_vol, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec,
@@ -647,9 +648,11 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
         // beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
         LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward_lsqr(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p,
                                                               ctx->r, ls->fwd, ctx->q, ctx->aw, ctx->part_fwd, st, SL(ctx)));
-        LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ctx->omega, l2p,
-                                                       ctx->c, nullptr, ctx->s, ls->ureg, ctx->part_vol, st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ls->ureg, st,
+                                                           SL(ctx)));
         cur ^= 1;
+        LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, z[cur], ctx->omega, l2p, ctx->c, nullptr,
+                                                       ctx->s, ls->ureg, ctx->part_vol, st, SL(ctx)));
         LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 0, ctx->part_fwd, ctx->n_part_fwd,
                                                                    ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
         // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
