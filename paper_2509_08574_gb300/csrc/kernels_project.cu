@@ -288,44 +288,61 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
     }
     const int nvm1 = G.nv - 1;
     const int h0 = __ldg(hit_ptr + cell), h1 = __ldg(hit_ptr + cell + 1);
-    for (int h = h0; h < h1; ++h) {
-        const CellHit e = __ldg(hits + h);
-        const int j = e.x >> 16, iu = e.x & 0xffff;
-        const float sa = __int_as_float(e.y), sb = __int_as_float(e.z);
-        const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 1);
-        const float s0 = cz.x, KD = cz.y, rKD = cz.w;
-        // candidate bounds only: the rows are then checked exactly
-        const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
-        const RT *rsc = rs + (long long)j * G.sj + (long long)iu * G.su;
-        const RT *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
+    // The crossing constants are the same for every thread of the CTA: each
+    // chunk of kGatherThreads crossings is prepared once, one per thread, in
+    // shared memory ({sa, sb, s0, KD} and {1/G(sa), 1/G(sb), ray offset}).
+    __shared__ float4 hc_a[kGatherThreads], hc_b[kGatherThreads];
+    for (int hb = h0; hb < h1; hb += kGatherThreads) {
+        const int nh = min(kGatherThreads, h1 - hb);
+        __syncthreads();  // the previous chunk has been read
+        if ((int)threadIdx.x < nh) {
+            const CellHit e = __ldg(hits + hb + threadIdx.x);
+            const int j = e.x >> 16, iu = e.x & 0xffff;
+            const float sa = __int_as_float(e.y), sb = __int_as_float(e.z);
+            const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 1);
+            const float s0 = cz.x, KD = cz.y, rKD = cz.w;
+            // candidate bounds only: the rows are then checked exactly
+            const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
+            const int roff = (int)((long long)j * G.sj + (long long)iu * G.su);  // N < 2^31
+            hc_a[threadIdx.x] = make_float4(sa, sb, s0, KD);
+            hc_b[threadIdx.x] = make_float4(rGa, rGb, __int_as_float(roff), 0.f);
+        }
+        __syncthreads();
+        for (int k = 0; k < nh; ++k) {
+            const float4 ca = hc_a[k], cb = hc_b[k];
+            const float sa = ca.x, sb = ca.y, s0 = ca.z, KD = ca.w;
+            const float rGa = cb.x, rGb = cb.y;
+            const RT *rsc = rs + __float_as_int(cb.z);
+            const RT *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
 #pragma unroll
-        for (int q = 0; q < L; ++q) {
-            const float zl = zlo[q], zh = zl + 1.f;
-            // G grows with s, so 1/G(sa) >= 1/G(sb); upper layers have zl >= 0
-            // except the middle layer of an odd nz (zl = -0.5)
-            const float vlo = zl * (zl >= 0.f ? rGb : rGa), vhi = zh * rGa;
-            int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
-            int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
-            ilo = max(ilo, 0);
-            ihi = pok[q] ? min(ihi, nvm1) : -1;
-            // only a layer touching z = 0 can hold the middle row of an odd nv
-            // (v = 0), which is its own mirror and belongs to the upper layer
-            const bool mid = zl < 1.f && (nvm1 & 1) == 0;
-            auto cand = [&](int iv) {
-                const float inv = KD * __ldg(vr + iv).y;
-                const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
-                // the ray is inside the layer between its two plane crossings
-                const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
-                if (len > 0.f) {
-                    accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
-                    if (!mid || 2 * iv != nvm1)
-                        accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
-                }
-            };
-            if (ilo <= ihi) cand(ilo);
-            if (ilo + 1 <= ihi) cand(ilo + 1);
-            if (ilo + 2 <= ihi) cand(ilo + 2);
-            for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
+            for (int q = 0; q < L; ++q) {
+                const float zl = zlo[q], zh = zl + 1.f;
+                // G grows with s, so 1/G(sa) >= 1/G(sb); upper layers have zl >= 0
+                // except the middle layer of an odd nz (zl = -0.5)
+                const float vlo = zl * (zl >= 0.f ? rGb : rGa), vhi = zh * rGa;
+                int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
+                int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
+                ilo = max(ilo, 0);
+                ihi = pok[q] ? min(ihi, nvm1) : -1;
+                // only a layer touching z = 0 can hold the middle row of an odd nv
+                // (v = 0), which is its own mirror and belongs to the upper layer
+                const bool mid = zl < 1.f && (nvm1 & 1) == 0;
+                auto cand = [&](int iv) {
+                    const float inv = KD * __ldg(vr + iv).y;
+                    const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
+                    // the ray is inside the layer between its two plane crossings
+                    const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
+                    if (len > 0.f) {
+                        accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
+                        if (!mid || 2 * iv != nvm1)
+                            accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
+                    }
+                };
+                if (ilo <= ihi) cand(ilo);
+                if (ilo + 1 <= ihi) cand(ilo + 1);
+                if (ilo + 2 <= ihi) cand(ilo + 2);
+                for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
+            }
         }
     }
     float *colv = vol + (long long)cell * G.nz;
