@@ -626,9 +626,9 @@ def run_serving(args):
                 "scans_per_s": args.requests / span, "makespan_s": span}
 
     # served: the request loop (FP32 storage, then BF16 storage with BF16 inputs)
-    def served_arm(bf16):
+    def served_arm(bf16, order=0):
         outs = outbufs()
-        srv = pk.Server(max_batch=8, max_running=2, use_graphs=True)
+        srv = pk.Server(max_batch=8, max_running=2, use_graphs=True, order=order)
         prm = []
         for k, (p, d) in enumerate(zip(pats, data)):
             srv.add_patient(k, p["geometry"], d["prior"])
@@ -663,11 +663,13 @@ def run_serving(args):
             raise RuntimeError("served request failed")
         res = summary([x["total_ms"] for x in st], span)
         res.update(max_batch=8, max_running=2, graphs=True, storage="bf16" if bf16 else "f32",
+                   order="fifo" if order == pk.ORDER_FIFO else "response_ratio",
                    mean_batch=args.requests / max(sstats["batches"] - warm["batches"], 1),
                    server=sstats)
         return res
 
     served, served16 = served_arm(False), served_arm(True)
+    served_fifo = served_arm(False, pk.ORDER_FIFO)
     plain = summary(lat_plain, span_plain)
     line = {
         "metric": "serving latency p50/p99 and scans/s (Poisson request stream, 16 patients)",
@@ -681,6 +683,7 @@ def run_serving(args):
                                  p["n_outer"] * p["n_inner"]] for p in pats]},
         "served": served,
         "served_bf16": served16,
+        "served_fifo": served_fifo,
         "plain_one_at_a_time": plain,
         "input_generation_s": t_in,
     }

@@ -19,7 +19,8 @@
  *   - order: among idle sessions with queued requests, the one whose oldest
  *     request has the highest response ratio (time waited + estimated device
  *     time) / estimated device time goes first, so short scans overtake long
- *     ones while no request waits without bound;
+ *     ones while no request waits without bound (or, if configured, the
+ *     oldest request first);
  *   - overlap: up to max_running batches (of different patients) are in
  *     flight at once, each on its session's own CUDA stream;
  *   - captured launches: a session records the launch sequence of each
@@ -49,7 +50,15 @@ typedef struct {
     int max_batch;      /* scans of one patient reconstructed together (1..64) */
     int max_running;    /* batches in flight at once (>= 1) */
     int use_graphs;     /* replay captured CUDA graphs (0: launch kernel by kernel) */
+    int order;          /* PICCS_ORDER_*: which idle session's queue goes next */
 } piccs_server_config;
+
+/* Issue order among idle sessions with queued requests: by the highest
+ * response ratio (time waited + estimated device time) / estimated device
+ * time of their oldest request (short scans overtake long ones; favours the
+ * median latency), or first come first served (the oldest request first;
+ * favours the tail when the device is overloaded). */
+enum { PICCS_ORDER_RESPONSE_RATIO = 0, PICCS_ORDER_FIFO = 1 };
 
 typedef struct {
     int status;          /* PICCS_OK or the request's error (PICCS_E*) */

@@ -32,6 +32,7 @@ WEIGHT_R1, WEIGHT_R2 = 0, 1
 X0_PRIOR, X0_ZERO, X0_USER = 0, 1, 2
 SOLVER_CGLS, SOLVER_LSQR, SOLVER_LSQR_REORTH = 0, 1, 2
 STORAGE_F32, STORAGE_BF16 = 0, 1
+ORDER_RESPONSE_RATIO, ORDER_FIFO = 0, 1
 
 _NAMES = {0: "PICCS_OK", -1: "PICCS_EINVAL", -2: "PICCS_ENOMEM", -3: "PICCS_ENONFINITE",
           -4: "PICCS_EBREAKDOWN", -5: "PICCS_ETIMEOUT", -6: "PICCS_ECUDA", -7: "PICCS_ENOTIMPL"}
@@ -67,7 +68,7 @@ class piccs_stats(C.Structure):
 
 class piccs_server_config(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("max_running", C.c_int),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("order", C.c_int)]
 
 
 class piccs_request_stats(C.Structure):
@@ -504,9 +505,9 @@ class Server:
     by HBM footprint, continuous batching, overlapped batches, CUDA graphs.
     Buffers handed to submit() are kept referenced until wait() returns."""
 
-    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True):
+    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True, order=0):
         cfg = piccs_server_config(int(hbm_budget), int(max_batch), int(max_running),
-                                  1 if use_graphs else 0)
+                                  1 if use_graphs else 0, int(order))
         h = C.c_void_p()
         _check_srv(_lib.piccs_server_create(C.byref(h), C.byref(cfg)), None)
         self.h = h.value

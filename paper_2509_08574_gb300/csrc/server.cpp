@@ -336,13 +336,15 @@ void worker_main(piccs_server *srv)
         while (progress && running < srv->cfg.max_running) {
             progress = false;
             Session *best = nullptr;
-            double best_ratio = -1.0;
+            double best_ratio = -1e300;
             const auto now = Clock::now();
             for (auto &kv : srv->sessions) {
                 Session &s = kv.second;
                 if (!s.running.empty() || s.queue.empty()) continue;
                 const Request *h = s.queue.front();
-                const double ratio = (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms;
+                const double ratio = srv->cfg.order == PICCS_ORDER_FIFO
+                                         ? -(double)h->id  // oldest first
+                                         : (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms;
                 if (ratio > best_ratio) {
                     best_ratio = ratio;
                     best = &s;
@@ -401,6 +403,8 @@ int piccs_server_create(piccs_server **out, const piccs_server_config *cfg)
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > 64) return fail(nullptr, PICCS_EINVAL, "max_batch must be in [1, 64]");
     if (cfg->max_running < 1) return fail(nullptr, PICCS_EINVAL, "max_running must be >= 1");
+    if (cfg->order != PICCS_ORDER_RESPONSE_RATIO && cfg->order != PICCS_ORDER_FIFO)
+        return fail(nullptr, PICCS_EINVAL, "unknown order %d", cfg->order);
     piccs_server *srv = new (std::nothrow) piccs_server();
     if (!srv) return fail(nullptr, PICCS_ENOMEM, "host allocation failed");
     srv->cfg = *cfg;
