@@ -22,7 +22,10 @@
  *     ones while no request waits without bound (or, if configured, the
  *     oldest request first);
  *   - overlap: up to max_running batches (of different patients) are in
- *     flight at once, each on its session's own CUDA stream;
+ *     flight at once, each on its session's own CUDA stream, as long as each
+ *     is small (estimated below 25 ms of device time per scan); a scan that
+ *     fills the GPU on its own runs alone, since overlapping it would only
+ *     stretch both batches;
  *   - captured launches: a session records the launch sequence of each
  *     (parameters, batch size) pair once as a CUDA graph and replays it.
  *

@@ -218,6 +218,10 @@ double estimate_ms(const piccs_geometry &g, const piccs_params &p)
     return its * (N * (g.nx + g.ny) + 20.0 * M) / 1.2e9;
 }
 
+// A scan whose estimated device time reaches this fills the GPU on its own:
+// running a second batch beside it only stretches both.
+constexpr double kOverlapMs = 25.0;
+
 bool same_params(const piccs_params &a, const piccs_params &b)
 {
     return std::memcmp(&a, &b, sizeof a) == 0;
@@ -331,7 +335,12 @@ void worker_main(piccs_server *srv)
         // run first -- short scans go ahead of long ones, and a long scan's
         // ratio grows while it waits, so none waits without bound
         int running = 0;
-        for (auto &kv : srv->sessions) running += !kv.second.running.empty();
+        bool big_running = false;
+        for (auto &kv : srv->sessions)
+            if (!kv.second.running.empty()) {
+                running += 1;
+                big_running |= kv.second.running.front()->est_ms >= kOverlapMs;
+            }
         bool progress = true;
         while (progress && running < srv->cfg.max_running) {
             progress = false;
@@ -351,17 +360,27 @@ void worker_main(piccs_server *srv)
                 }
             }
             if (!best) break;
+            // batches overlap only while every one of them is small; the order
+            // is kept: nothing overtakes a large scan that is next
+            if (running > 0 && (big_running || best->queue.front()->est_ms >= kOverlapMs)) break;
             if (issue_batch(srv, *best)) {
                 progress = true;
-                running += !best->running.empty();
+                if (!best->running.empty()) {
+                    running += 1;
+                    big_running |= best->running.front()->est_ms >= kOverlapMs;
+                }
             } else {
                 // wait for memory: try sessions that are already resident
                 for (auto &kv : srv->sessions) {
                     Session &s = kv.second;
                     if (&s == best || !s.running.empty() || s.queue.empty() || !s.ctx) continue;
+                    if (running > 0 && (big_running || s.queue.front()->est_ms >= kOverlapMs)) continue;
                     if (issue_batch(srv, s)) {
                         progress = true;
-                        running += !s.running.empty();
+                        if (!s.running.empty()) {
+                            running += 1;
+                            big_running |= s.running.front()->est_ms >= kOverlapMs;
+                        }
                         break;
                     }
                 }
