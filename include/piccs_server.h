@@ -26,7 +26,8 @@
  *     is small (estimated below 25 ms of device time per scan); a scan that
  *     fills the GPU on its own runs alone, since overlapping it would only
  *     stretch both batches;
- *   - captured launches: a session records the launch sequence of each
+ *   - captured launches: for scans estimated below 200 ms (where launch
+ *     costs matter), a session records the launch sequence of each
  *     (parameters, batch size) pair once as a CUDA graph and replays it.
  *
  * All calls are thread-safe.  A worker thread owned by the server issues
@@ -52,7 +53,7 @@ typedef struct {
                            memory free when the server is created) */
     int max_batch;      /* scans of one patient reconstructed together (1..64) */
     int max_running;    /* batches in flight at once (>= 1) */
-    int use_graphs;     /* replay captured CUDA graphs (0: launch kernel by kernel) */
+    int use_graphs;     /* replay captured CUDA graphs for short scans (0: never) */
     int order;          /* PICCS_ORDER_*: which idle session's queue goes next */
 } piccs_server_config;
 

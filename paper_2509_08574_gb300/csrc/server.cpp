@@ -222,6 +222,11 @@ double estimate_ms(const piccs_geometry &g, const piccs_params &p)
 // running a second batch beside it only stretches both.
 constexpr double kOverlapMs = 25.0;
 
+// Graphs pay off where launches cost a noticeable part of a scan; for longer
+// scans the one-time capture of a new (parameters, batch size) pair would
+// only delay the batch.
+constexpr double kGraphMs = 200.0;
+
 bool same_params(const piccs_params &a, const piccs_params &b)
 {
     return std::memcmp(&a, &b, sizeof a) == 0;
@@ -259,7 +264,8 @@ bool issue_batch(piccs_server *srv, Session &s)
                      ? piccs_stage_bf16(s.ctx, i, batch[i]->h_proj, 1)
                      : piccs_stage(s.ctx, i, static_cast<const float *>(batch[i]->h_proj), 1);
     }
-    if (rc == PICCS_OK) rc = piccs_run_staged(s.ctx, n, &head->params, srv->cfg.use_graphs);
+    const bool graph = srv->cfg.use_graphs && head->est_ms < kGraphMs;
+    if (rc == PICCS_OK) rc = piccs_run_staged(s.ctx, n, &head->params, graph);
     for (int i = 0; i < n && rc == PICCS_OK; ++i) rc = piccs_unstage(s.ctx, i, batch[i]->h_out, 1);
     if (rc == PICCS_OK) {
         DoneArg *a = new (std::nothrow) DoneArg{srv, &s};
@@ -279,7 +285,7 @@ bool issue_batch(piccs_server *srv, Session &s)
     s.last_used = ++srv->tick;
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->st.batches += 1;
-    if (srv->cfg.use_graphs) srv->st.graph_replays += 1;
+    if (graph) srv->st.graph_replays += 1;
     return true;
 }
 

@@ -82,7 +82,7 @@ def test_served_results_equal_standalone(pk, patients, graphs):
     assert all(st["status"] == 0 for st in stats), stats
     assert s["completed"] == len(reqs) and s["failed"] == 0
     assert s["batches"] <= len(reqs)
-    if graphs:
+    if graphs:  # these scans are short: every batch replays a graph
         assert s["graph_replays"] == s["batches"]
     for (k, i, params), (_, out) in zip(reqs, tickets):
         g, prior, scans = patients[k]
