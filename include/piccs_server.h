@@ -15,7 +15,10 @@
  *   - continuous batching: when a session is idle, the requests queued for
  *     it that share parameters (up to max_batch) are reconstructed together,
  *     one launch per kernel for all of them; requests arriving meanwhile join
- *     the next batch;
+ *     the next batch.  Long scans (estimated 200 ms or more) are batched only
+ *     while more than 2 * max_batch requests are queued in all: they gain
+ *     little from sharing launches, and the first scan of a batch waits for
+ *     all of it;
  *   - order: among idle sessions with queued requests, the one whose oldest
  *     request has the highest response ratio (time waited + estimated device
  *     time) / estimated device time goes first, so short scans overtake long

@@ -233,7 +233,8 @@ bool same_params(const piccs_params &a, const piccs_params &b)
 }
 
 // Issues the next batch of session s; false if it has to wait for memory.
-bool issue_batch(piccs_server *srv, Session &s)
+// backlog: requests queued over all sessions.
+bool issue_batch(piccs_server *srv, Session &s, int backlog)
 {
     Request *head = s.queue.front();
     int rc = make_resident(srv, s, head->params);
@@ -246,7 +247,11 @@ bool issue_batch(piccs_server *srv, Session &s)
         finish_requests(srv, batch, rc);
         return true;
     }
-    for (auto it = s.queue.begin(); it != s.queue.end() && (int)batch.size() < srv->cfg.max_batch;) {
+    // A long scan gains little from sharing launches (the GPU is full either
+    // way) while the first scan of a batch waits for the whole batch: long
+    // scans are batched only to work off a deep backlog.
+    const int cap = head->est_ms < kGraphMs || backlog > 2 * srv->cfg.max_batch ? srv->cfg.max_batch : 1;
+    for (auto it = s.queue.begin(); it != s.queue.end() && (int)batch.size() < cap;) {
         if (same_params((*it)->params, head->params)) {
             batch.push_back(*it);
             it = s.queue.erase(it);
@@ -347,6 +352,8 @@ void worker_main(piccs_server *srv)
                 running += 1;
                 big_running |= kv.second.running.front()->est_ms >= kOverlapMs;
             }
+        int backlog = 0;
+        for (auto &kv : srv->sessions) backlog += (int)kv.second.queue.size();
         bool progress = true;
         while (progress && running < srv->cfg.max_running) {
             progress = false;
@@ -369,7 +376,7 @@ void worker_main(piccs_server *srv)
             // batches overlap only while every one of them is small; the order
             // is kept: nothing overtakes a large scan that is next
             if (running > 0 && (big_running || best->queue.front()->est_ms >= kOverlapMs)) break;
-            if (issue_batch(srv, *best)) {
+            if (issue_batch(srv, *best, backlog)) {
                 progress = true;
                 if (!best->running.empty()) {
                     running += 1;
@@ -381,7 +388,7 @@ void worker_main(piccs_server *srv)
                     Session &s = kv.second;
                     if (&s == best || !s.running.empty() || s.queue.empty() || !s.ctx) continue;
                     if (running > 0 && (big_running || s.queue.front()->est_ms >= kOverlapMs)) continue;
-                    if (issue_batch(srv, s)) {
+                    if (issue_batch(srv, s, backlog)) {
                         progress = true;
                         if (!s.running.empty()) {
                             running += 1;
