@@ -626,7 +626,7 @@ def run_serving(args):
                 "scans_per_s": args.requests / span, "makespan_s": span}
 
     # served: the request loop (FP32 storage, then BF16 storage with BF16 inputs)
-    def served_arm(bf16, order=0):
+    def served_arm(bf16, order=pk.ORDER_ADAPTIVE):
         outs = outbufs()
         srv = pk.Server(max_batch=8, max_running=2, use_graphs=True, order=order)
         prm = []
@@ -663,13 +663,14 @@ def run_serving(args):
             raise RuntimeError("served request failed")
         res = summary([x["total_ms"] for x in st], span)
         res.update(max_batch=8, max_running=2, graphs=True, storage="bf16" if bf16 else "f32",
-                   order="fifo" if order == pk.ORDER_FIFO else "response_ratio",
+                   order={pk.ORDER_FIFO: "fifo", pk.ORDER_RESPONSE_RATIO: "response_ratio"}.get(
+                       order, "adaptive"),
                    mean_batch=args.requests / max(sstats["batches"] - warm["batches"], 1),
                    server=sstats)
         return res
 
     served, served16 = served_arm(False), served_arm(True)
-    served_fifo = served_arm(False, pk.ORDER_FIFO)
+    served_rr = served_arm(False, pk.ORDER_RESPONSE_RATIO)
     plain = summary(lat_plain, span_plain)
     line = {
         "metric": "serving latency p50/p99 and scans/s (Poisson request stream, 16 patients)",
@@ -683,7 +684,7 @@ def run_serving(args):
                                  p["n_outer"] * p["n_inner"]] for p in pats]},
         "served": served,
         "served_bf16": served16,
-        "served_fifo": served_fifo,
+        "served_response_ratio": served_rr,
         "plain_one_at_a_time": plain,
         "input_generation_s": t_in,
     }

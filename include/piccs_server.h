@@ -22,8 +22,8 @@
  *   - order: among idle sessions with queued requests, the one whose oldest
  *     request has the highest response ratio (time waited + estimated device
  *     time) / estimated device time goes first, so short scans overtake long
- *     ones while no request waits without bound (or, if configured, the
- *     oldest request first);
+ *     ones while no request waits without bound -- or the oldest request
+ *     first, or (adaptive) the former only under a backlog;
  *   - overlap: up to max_running batches (of different patients) are in
  *     flight at once, each on its session's own CUDA stream, as long as each
  *     is small (estimated below 25 ms of device time per scan); a scan that
@@ -63,9 +63,11 @@ typedef struct {
 /* Issue order among idle sessions with queued requests: by the highest
  * response ratio (time waited + estimated device time) / estimated device
  * time of their oldest request (short scans overtake long ones; favours the
- * median latency), or first come first served (the oldest request first;
- * favours the tail when the device is overloaded). */
-enum { PICCS_ORDER_RESPONSE_RATIO = 0, PICCS_ORDER_FIFO = 1 };
+ * median latency), first come first served (the oldest request first), or
+ * adaptive: response ratio while more than 2 * max_batch requests are
+ * queued (a backlog worth reordering), first come first served otherwise
+ * (with a short queue, reordering only makes the overtaken scan wait). */
+enum { PICCS_ORDER_RESPONSE_RATIO = 0, PICCS_ORDER_FIFO = 1, PICCS_ORDER_ADAPTIVE = 2 };
 
 typedef struct {
     int status;          /* PICCS_OK or the request's error (PICCS_E*) */

@@ -32,7 +32,7 @@ WEIGHT_R1, WEIGHT_R2 = 0, 1
 X0_PRIOR, X0_ZERO, X0_USER = 0, 1, 2
 SOLVER_CGLS, SOLVER_LSQR, SOLVER_LSQR_REORTH = 0, 1, 2
 STORAGE_F32, STORAGE_BF16 = 0, 1
-ORDER_RESPONSE_RATIO, ORDER_FIFO = 0, 1
+ORDER_RESPONSE_RATIO, ORDER_FIFO, ORDER_ADAPTIVE = 0, 1, 2
 
 _NAMES = {0: "PICCS_OK", -1: "PICCS_EINVAL", -2: "PICCS_ENOMEM", -3: "PICCS_ENONFINITE",
           -4: "PICCS_EBREAKDOWN", -5: "PICCS_ETIMEOUT", -6: "PICCS_ECUDA", -7: "PICCS_ENOTIMPL"}
@@ -505,7 +505,7 @@ class Server:
     by HBM footprint, continuous batching, overlapped batches, CUDA graphs.
     Buffers handed to submit() are kept referenced until wait() returns."""
 
-    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True, order=0):
+    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True, order=2):
         cfg = piccs_server_config(int(hbm_budget), int(max_batch), int(max_running),
                                   1 if use_graphs else 0, int(order))
         h = C.c_void_p()

@@ -354,6 +354,8 @@ void worker_main(piccs_server *srv)
             }
         int backlog = 0;
         for (auto &kv : srv->sessions) backlog += (int)kv.second.queue.size();
+        const bool by_ratio = srv->cfg.order == PICCS_ORDER_RESPONSE_RATIO ||
+                              (srv->cfg.order == PICCS_ORDER_ADAPTIVE && backlog > 2 * srv->cfg.max_batch);
         bool progress = true;
         while (progress && running < srv->cfg.max_running) {
             progress = false;
@@ -364,9 +366,8 @@ void worker_main(piccs_server *srv)
                 Session &s = kv.second;
                 if (!s.running.empty() || s.queue.empty()) continue;
                 const Request *h = s.queue.front();
-                const double ratio = srv->cfg.order == PICCS_ORDER_FIFO
-                                         ? -(double)h->id  // oldest first
-                                         : (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms;
+                const double ratio = !by_ratio ? -(double)h->id  // oldest first
+                                               : (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms;
                 if (ratio > best_ratio) {
                     best_ratio = ratio;
                     best = &s;
@@ -435,7 +436,7 @@ int piccs_server_create(piccs_server **out, const piccs_server_config *cfg)
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > 64) return fail(nullptr, PICCS_EINVAL, "max_batch must be in [1, 64]");
     if (cfg->max_running < 1) return fail(nullptr, PICCS_EINVAL, "max_running must be >= 1");
-    if (cfg->order != PICCS_ORDER_RESPONSE_RATIO && cfg->order != PICCS_ORDER_FIFO)
+    if (cfg->order < PICCS_ORDER_RESPONSE_RATIO || cfg->order > PICCS_ORDER_ADAPTIVE)
         return fail(nullptr, PICCS_EINVAL, "unknown order %d", cfg->order);
     piccs_server *srv = new (std::nothrow) piccs_server();
     if (!srv) return fail(nullptr, PICCS_ENOMEM, "host allocation failed");
