@@ -262,11 +262,14 @@ size_t basis_vec_bytes(const piccs_geometry *g, int n_inner, int storage)
     return align256(nv * (size_t)lsqr_basis_stride((long long)M) * es);
 }
 
-// per slot: the vectors (FP32 or BF16), then the Gram-Schmidt partial sums
+// Gram-Schmidt partial sums of one slot (a fixed size)
+size_t basis_dots_bytes() { return align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double)); }
+
+// per slot: the Gram-Schmidt partial sums, then the vectors (FP32 or BF16), so
+// that a region sized for one (n_inner, storage) serves every smaller one
 size_t basis_bytes(const piccs_geometry *g, int n_inner, int storage)
 {
-    return basis_vec_bytes(g, n_inner, storage) +
-           align256((size_t)kMaxBasis * lsqr_dot_blocks() * sizeof(double));
+    return basis_dots_bytes() + basis_vec_bytes(g, n_inner, storage);
 }
 
 }  // namespace
@@ -430,7 +433,7 @@ void piccs_destroy(piccs_ctx *ctx)
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    cudaFree(ctx->basis);
+    cudaFree(ctx->part_dots);  // the basis region starts with the partial sums
     cudaFree(ctx->base);
     delete ctx;
 }
@@ -583,8 +586,7 @@ int piccs_reg_normal(piccs_ctx *ctx, const float *d_omega, const piccs_params *p
 static int ensure_basis(piccs_ctx *ctx, int n_inner, int storage)
 {
     const size_t per_slot = basis_bytes(&ctx->geo, n_inner, storage);
-    const size_t vec_bytes = basis_vec_bytes(&ctx->geo, n_inner, storage);
-    if (ctx->basis && ctx->basis_stride == per_slot) return PICCS_OK;
+    if (ctx->basis && per_slot <= ctx->basis_stride) return PICCS_OK;  // large enough
     const size_t bytes = per_slot * ctx->nslot;
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
@@ -592,7 +594,10 @@ static int ensure_basis(piccs_ctx *ctx, int n_inner, int storage)
     if (bytes > free_b + held)
         return set_err(ctx, PICCS_ENOMEM, "LSQR basis needs %zu bytes, %zu free", bytes, free_b + held);
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaFree(ctx->basis);
+    // captured graphs hold the old basis pointers and stride
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.exec);
+    ctx->graphs.clear();
+    if (ctx->part_dots) cudaFree(ctx->part_dots);
     ctx->basis = nullptr;
     ctx->part_dots = nullptr;
     ctx->basis_stride = 0;
@@ -601,8 +606,8 @@ static int ensure_basis(piccs_ctx *ctx, int n_inner, int storage)
         cudaGetLastError();
         return set_err(ctx, PICCS_ENOMEM, "cudaMalloc of the LSQR basis (%zu bytes) failed", bytes);
     }
-    ctx->basis = mem;
-    ctx->part_dots = reinterpret_cast<double *>(static_cast<char *>(mem) + vec_bytes);
+    ctx->part_dots = static_cast<double *>(mem);
+    ctx->basis = static_cast<char *>(mem) + basis_dots_bytes();
     ctx->basis_stride = per_slot;
     return PICCS_OK;
 }

@@ -161,3 +161,25 @@ def test_lsqr_c2_first_iterations_match_oracle(pk):
                       scan.alpha, scan.lam, scan.tau, 1, 3, solver=O.SOLVER_LSQR)
     assert rel_l2(x, ref) <= TOL_X
     assert rel_l2(x - xp, ref - xp) <= 2e-2
+
+
+def test_staged_graphs_follow_basis_reallocation(pk, c1):
+    """Graph-replayed re-orthogonalised runs with a small basis, then a larger
+    one (the basis is reallocated, the captured graphs are dropped), then the
+    small one again: every run equals a fresh reconstruction."""
+    scan, b, xp = c1
+    g = scan.geometry
+    runs = [pk.make_params(0.5, 0.5, scan.tau, 1, n, solver=2, storage=st)
+            for n, st in ((4, 0), (8, 0), (4, 0), (8, 1), (4, 0))]
+    with pk.Context(g) as ctx:
+        ctx.set_prior_broadcast(xp)
+        for params in runs:
+            out = torch.empty(g.vol_shape(), dtype=torch.float32).pin_memory()
+            ctx.stage(0, torch.from_numpy(b).pin_memory())
+            ctx.run_staged(1, params, graph=True)
+            ctx.unstage(0, out)
+            torch.cuda.synchronize()
+            with pk.Context(g) as fresh:
+                fresh.set_prior(_dev(xp))
+                ref = fresh.reconstruct(_dev(b), params).cpu()
+            assert torch.equal(out, ref), (params.n_inner, params.storage)
