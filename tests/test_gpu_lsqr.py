@@ -171,11 +171,12 @@ def test_staged_graphs_follow_basis_reallocation(pk, c1):
     g = scan.geometry
     runs = [pk.make_params(0.5, 0.5, scan.tau, 1, n, solver=2, storage=st)
             for n, st in ((4, 0), (8, 0), (4, 0), (8, 1), (4, 0))]
+    hb = torch.from_numpy(b).pin_memory()  # held until the asynchronous copies are done
     with pk.Context(g) as ctx:
         ctx.set_prior_broadcast(xp)
         for params in runs:
             out = torch.empty(g.vol_shape(), dtype=torch.float32).pin_memory()
-            ctx.stage(0, torch.from_numpy(b).pin_memory())
+            ctx.stage(0, hb)
             ctx.run_staged(1, params, graph=True)
             ctx.unstage(0, out)
             torch.cuda.synchronize()

@@ -86,7 +86,8 @@ def test_bf16_host_input_equals_device_rounding(pk, c1):
         torch.cuda.synchronize()
         assert torch.equal(out, x_dev)
         # FP32 staging with a BF16 run rounds on the device: same result again
-        ctx.stage(0, torch.from_numpy(b).pin_memory())
+        hb = torch.from_numpy(b).pin_memory()  # held until the asynchronous copy is done
+        ctx.stage(0, hb)
         ctx.run_staged(1, params, graph=True)
         out2 = torch.empty_like(out).pin_memory()
         ctx.unstage(0, out2)
