@@ -92,7 +92,8 @@ int piccs_server_create(piccs_server **out, const piccs_server_config *cfg);
 /* Finish every queued request, stop the worker, free all sessions. */
 void piccs_server_destroy(piccs_server *srv);
 
-/* Message of the last failing call on srv (NULL srv: of piccs_server_create). */
+/* Message of the last failing call on srv (NULL srv: of piccs_server_create
+ * on this thread); valid until this thread's next call of this function. */
 const char *piccs_server_last_error(const piccs_server *srv);
 
 /* Register patient `patient` (any int not yet registered): its geometry and

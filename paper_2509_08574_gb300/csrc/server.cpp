@@ -427,7 +427,12 @@ extern "C" {
 
 const char *piccs_server_last_error(const piccs_server *srv)
 {
-    return srv ? srv->err.c_str() : g_create_err.c_str();
+    if (!srv) return g_create_err.c_str();
+    // the message may be replaced by another thread: hand out a per-thread copy
+    thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(const_cast<piccs_server *>(srv)->mu);
+    copy = srv->err;
+    return copy.c_str();
 }
 
 int piccs_server_create(piccs_server **out, const piccs_server_config *cfg)
