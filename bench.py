@@ -10,6 +10,13 @@ work) in this repository's CUDA kernels, inputs resident in HBM.
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.  Under torchrun every rank
 runs an independent replica on its own GPU (the path has no exchange step).
+
+Other measurements: `--solver lsqr|lsqr_reorth` (the inner solver),
+`--storage bf16` (mixed precision, with its image error against FP32 and the
+ground truth), `--batch B` (B scans per launch sequence), `--workload` (the
+64^3, 512^3 and C-arm configurations), `--kernels-only` (the hot kernels
+alone, for profiler captures) and `--serving` (a Poisson request stream over
+16 patients through the request server against one scan at a time).
 """
 from __future__ import annotations
 

@@ -1,9 +1,11 @@
-// Krylov (CGLS) vector work for sm_103a: the fused vector updates, the
-// FP64 reductions and the scalar recurrences of one CGLS step on the
-// augmented IRN-PICCS system (Sec. 2.3; CGLS is the inner solver the paper
-// uses, mathematically equivalent to LSQR).
+// Krylov vector work for sm_103a: the fused vector updates, the FP64
+// reductions and the scalar recurrences of one step of CGLS or of LSQR
+// (Golub-Kahan bidiagonalisation with the Givens QR update, optionally
+// re-orthogonalised) on the augmented IRN-PICCS system (Sec. 2.3 names both,
+// as mathematically equivalent).
 //
-// The scalars (gamma, delta, step, beta) live in device memory and are read
+// The scalars (CGLS: gamma, delta, step, beta; LSQR: see LsqrScalars in
+// internal.h) live in device memory and are read
 // by the vector kernels directly, so one reconstruction enqueues its whole
 // iteration sequence without a host round trip.  Reductions are two-level and
 // deterministic: each kernel writes one FP64 partial per CTA, and a one-CTA
