@@ -35,6 +35,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace piccs {
@@ -327,21 +329,32 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                 // only a layer touching z = 0 can hold the middle row of an odd nv
                 // (v = 0), which is its own mirror and belongs to the upper layer
                 const bool mid = zl < 1.f && (nvm1 & 1) == 0;
-                auto cand = [&](int iv) {
-                    const float inv = KD * __ldg(vr + iv).y;
-                    const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
-                    // the ray is inside the layer between its two plane crossings
-                    const float len = fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
-                    if (len > 0.f) {
-                        accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
-                        if (!mid || 2 * iv != nvm1)
-                            accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
-                    }
+                // ORDERED: the layer lies above z = 0 (zl >= 0), so every
+                // candidate row has v >= 0, 1/v > 0 and enters the layer's lower
+                // plane before its upper one (xl <= xh, FP32 rounding is monotone)
+                auto rows = [&](auto ordered) {
+                    auto cand = [&](int iv) {
+                        const float inv = KD * __ldg(vr + iv).y;
+                        const float xl = fmaf(zl, inv, -s0), xh = fmaf(zh, inv, -s0);
+                        // the ray is inside the layer between its two plane crossings
+                        const float len = decltype(ordered)::value
+                                              ? fminf(sb, xh) - fmaxf(sa, xl)
+                                              : fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
+                        if (len > 0.f) {
+                            accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
+                            if (!mid || 2 * iv != nvm1)
+                                accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
+                        }
+                    };
+                    if (ilo <= ihi) cand(ilo);
+                    if (ilo + 1 <= ihi) cand(ilo + 1);
+                    if (ilo + 2 <= ihi) cand(ilo + 2);
+                    for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
                 };
-                if (ilo <= ihi) cand(ilo);
-                if (ilo + 1 <= ihi) cand(ilo + 1);
-                if (ilo + 2 <= ihi) cand(ilo + 2);
-                for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
+                if (zl >= 0.f)
+                    rows(std::true_type{});
+                else
+                    rows(std::false_type{});
             }
         }
     }
