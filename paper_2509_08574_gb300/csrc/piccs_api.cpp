@@ -119,7 +119,8 @@ struct Launch {
     cudaEvent_t a = nullptr;
     Launch(piccs_ctx *c, int k) : ctx(c), kind(k)
     {
-        ctx->launches[kind] += 1;
+        // the backprojection is two kernels (ray scaling, gather)
+        ctx->launches[kind] += kind == PICCS_KERNEL_ADJOINT ? 2 : 1;
         if (ctx->timing) {
             a = take_event(ctx);
             if (a) cudaEventRecord(a, ctx->stream);
