@@ -47,7 +47,9 @@ SOLVERS = {"cgls": (0, "CGLS"), "lsqr": (1, "LSQR"), "lsqr_reorth": (2, "re-orth
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--seeds", type=int, default=10,
+                    help="distinct noise draws of the scan the timed steps rotate through")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -333,7 +335,11 @@ def run_ours(args):
         b, xp, truth = synth_inputs(scan, pk, torch)
         b_np = xp_np = None
     else:
-        b_np = scan.measured()
+        # the analytic line integrals once, then one Poisson draw per seed
+        li = P.project_analytic(scan.scan_phantom, g)
+        draws = [P.poisson_log_data(li, scan.I0, scan.noise_seed + k).astype(np.float32)
+                 for k in range(max(1, args.seeds))]
+        b_np = draws[0]
         xp_np = scan.prior_volume(ss=1)
         b = torch.from_numpy(b_np).cuda()
         xp = torch.from_numpy(xp_np).cuda()
@@ -345,6 +351,12 @@ def run_ours(args):
         b = b.unsqueeze(0).expand((B,) + tuple(b.shape)).contiguous()
         xp = xp.unsqueeze(0).expand((B,) + tuple(xp.shape)).contiguous()
     out = torch.empty(((B,) if B > 1 else ()) + g.vol_shape(), dtype=torch.float32, device="cuda")
+    # the timed steps rotate through the noise draws (one scan's worth each)
+    inputs = [b]
+    if b_np is not None and args.seeds > 1:
+        for d in draws[1:]:
+            t = torch.from_numpy(d).cuda()
+            inputs.append(t.unsqueeze(0).expand((B,) + tuple(t.shape)).contiguous() if B > 1 else t)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     storage = pk.STORAGE_BF16 if args.storage == "bf16" else pk.STORAGE_F32
     params = pk.make_params(scan.alpha, scan.lam, scan.tau, scan.n_outer, scan.n_inner,
@@ -363,6 +375,11 @@ def run_ours(args):
         if rep.status != 0 or rep.iterations_run != scan.iterations:
             raise RuntimeError(f"reconstruction {slot}: status {rep.status}, "
                                f"{rep.iterations_run} iterations")
+    with torch.cuda.stream(stream):  # every noise draw reconstructs cleanly too
+        for inp in inputs[1:]:
+            ctx.reconstruct(inp, params, out=out)
+            if ctx.report().status != 0:
+                raise RuntimeError("reconstruction of a noise draw failed")
 
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -377,7 +394,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.zero_()  # outside the step's events: L2 holds no input at step start
             ev[k][0].record(stream)
-            ctx.reconstruct(b, params, out=out)
+            ctx.reconstruct(inputs[k % len(inputs)], params, out=out)
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -432,7 +449,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(scan, args.solver,
                                        pk.piccs_query_workspace_batched(g, params, B)),
-                       batch=B, storage=args.storage,
+                       batch=B, storage=args.storage, noise_draws=len(inputs),
                        value=("whole-job ms per scan: p50 step time (max over ranks) / "
                               "(ranks x scans per step); p50_ms/p99_ms: one replica's ms per scan")),
         "p50_ms": p50, "p99_ms": p99,
