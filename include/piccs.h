@@ -31,8 +31,10 @@
  *     address space, h_* are host pointers.  The caller owns them; the library
  *     never frees or keeps them after the call returns (except d_* buffers
  *     read asynchronously, which must stay valid until the stream work ends).
- *     Device buffers must be 16-byte aligned (cudaMalloc/torch allocations
- *     are); misaligned buffers are still accepted but take slower paths.
+ *     Caller buffers need only the alignment of their element type: the
+ *     kernels read and write them element by element, and whole-vector moves
+ *     go through cudaMemcpy into the context's own (256-byte aligned)
+ *     workspace, where the vectorised kernels work.
  *   - Every call that launches work enqueues it on the context's stream and
  *     returns without waiting, unless its comment says it synchronises.
  *   - Return value: PICCS_OK (0) or a negative PICCS_E* code; nothing is

@@ -243,8 +243,6 @@ Layout plan(const piccs_geometry *g, int nslot = 1)
 
 constexpr int kMaxSlots = 64;
 
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
 template <class T>
 T *slot_at(T *p, const piccs_ctx *ctx, int s)
 {
