@@ -10,7 +10,7 @@
  *   replaces each TV term by a weighted 2-norm whose weights
  *   W(Dz)_ii = (sqrt(sum_d [D_d z]_i^2) + tau^2)^(-1/2) are frozen at the
  *   previous outer iterate, and solves each reweighted problem approximately
- *   with a few CGLS iterations on the augmented least-squares system
+ *   with a few CGLS (or LSQR) iterations on the augmented least-squares system
  *   [A; alpha W1 D; lambda W2 D] x ~ [b; 0; lambda W2 D x_p] (the display after
  *   Eq. 11), warm-started at the previous iterate.
  *
@@ -76,12 +76,14 @@ enum { PICCS_X0_PRIOR = 0, PICCS_X0_ZERO = 1, PICCS_X0_USER = 2 };
 
 /* Inner Krylov solver (Sec. 2.3: LSQR, or the mathematically equivalent
  * CGLS).  CGLS: Hestenes-Stiefel recurrences.  LSQR: Golub-Kahan
- * bidiagonalisation of the augmented operator with a Givens QR update (one
- * more forward projection per cycle than CGLS).  LSQR_REORTH: LSQR with each
- * new v re-orthogonalised against the cycle's earlier ones (classical
- * Gram-Schmidt, twice); the first such reconstruction on a context allocates
- * (n_inner - 1) * M floats for the basis (PICCS_ENOMEM if the device lacks
- * them) and keeps them; n_inner - 1 must not exceed 256. */
+ * bidiagonalisation of the augmented operator with a Givens QR update; the
+ * data residual is kept current through A w, so it takes as many projections
+ * as CGLS.  LSQR_REORTH: LSQR with each new v re-orthogonalised against the
+ * cycle's earlier ones (classical Gram-Schmidt, twice); the first such
+ * reconstruction on a context allocates the basis, (n_inner - 1) * M values
+ * per scan (FP32, or BF16 with PICCS_STORAGE_BF16; PICCS_ENOMEM if the device
+ * lacks them), keeps it and grows it when a later one needs more; n_inner - 1
+ * must not exceed 256. */
 enum { PICCS_SOLVER_CGLS = 0, PICCS_SOLVER_LSQR = 1, PICCS_SOLVER_LSQR_REORTH = 2 };
 
 /* Storage precision.  F32: every vector in FP32.  BF16: the measured
@@ -110,7 +112,7 @@ typedef struct {
     float alpha, lambda;       /* regularisation parameters (>= 0), Eq. 3 */
     float tau;                 /* smoothing parameter (> 0), the weight equation */
     int n_outer;               /* IRN reweighting cycles (>= 1) */
-    int n_inner;               /* CGLS iterations per cycle (>= 0);
+    int n_inner;               /* Krylov iterations per cycle (>= 0);
                                   total iterations = n_outer * n_inner */
     int x0_mode;               /* PICCS_X0_* */
     int variant;               /* PICCS_VARIANT_* */
