@@ -227,8 +227,12 @@ int piccs_report_slot(piccs_ctx *ctx, int slot, piccs_stats *out);
  * their staged projections (x0_mode PRIOR or ZERO); piccs_unstage copies slot
  * `slot`'s volume out.  All three are asynchronous on the context's stream
  * (host buffers should be pinned).  use_graph != 0: the launch sequence of a
- * (params, nactive) pair is captured once as a CUDA graph and replayed (the
- * per-step scalars stay on the device, so a replay is a full reconstruction). */
+ * (params, nactive) pair is captured once as a CUDA graph (on a private
+ * stream; the legacy default stream cannot be captured) and replayed on the
+ * context's stream -- the per-step scalars stay on the device, so a replay is
+ * a full reconstruction; growing the LSQR basis drops the captured graphs.
+ * Not with profiling timing on (piccs_profile_enable), which launches
+ * kernel by kernel. */
 int piccs_set_prior_broadcast(piccs_ctx *ctx, const float *xprior, int from_host);
 int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host);
 /* The same with projections already in BF16 (N values, bfloat16 bit
