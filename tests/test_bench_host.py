@@ -82,3 +82,49 @@ def test_parse_clock_csv():
     assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
     assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 3
     assert bench.parse_clock_csv("") is None
+
+
+def test_golden_nnz_count_is_the_oracles():
+    """The roofline's algorithmic unit comes from tests/golden/nnz_counts.json;
+    the 64^3 entry is recounted here with the oracle's walk."""
+    import json
+    import oracle as O
+    import phantoms as P
+
+    with open(os.path.join(ROOT, "tests", "golden", "nnz_counts.json")) as f:
+        golden = json.load(f)
+    scan = P.c1_small()
+    rec = golden[scan.name]
+    assert rec["M"] == scan.geometry.M and rec["N"] == scan.geometry.N
+    assert O.count_nnz(scan.geometry) == rec["nnz"]
+    for name, r in golden.items():  # every pieces count is at least one per hit ray and voxel
+        assert r["nnz"] > max(r["M"], r["N"]) // 2, name
+
+
+def test_code_digest_ignores_comments_only(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(float *x) {\n    x[0] = 1.f;  // one\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("/* other\n header */\n\n__global__ void k(float *x) {\n    x[0] = 1.f;\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("__global__ void k(float *x) {\n    x[0] = 2.f;\n}\n")
+    assert bench.code_digest(str(a)) == bench.code_digest(str(b))
+    assert bench.code_digest(str(a)) != bench.code_digest(str(c))
+
+
+def test_serving_patients_are_valid_and_seeded():
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2509_08574_gb300 as pk
+
+    pats = bench.serving_patients()
+    assert len(pats) == 16
+    assert [p["geometry"].nx for p in pats] == [p["geometry"].nx for p in bench.serving_patients()]
+    for p in pats:
+        g = p["geometry"]
+        assert g.nx in (128, 256, 384) and 30 <= g.n_views <= 120 and 256 <= g.nu <= 768
+        assert 20 <= p["n_outer"] * p["n_inner"] <= 40
+        pk.piccs_validate(g, pk.make_params(n_outer=p["n_outer"], n_inner=p["n_inner"]))
