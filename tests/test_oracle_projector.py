@@ -122,6 +122,17 @@ def test_adjoint_by_voxel_clipping_matches_walk():
     np.testing.assert_allclose(O.adjoint_voxels(g, y, vox), full, rtol=0, atol=1e-12)
 
 
+def test_clip_ray_voxel_matches_bruteforce_clipping():
+    """The oracle's single ray/voxel clip (the primitive behind its per-voxel
+    adjoint) equals the numpy slab clip of the same pair, on every pair of a
+    tiny geometry, hits and misses alike."""
+    g = P.tiny_geometry(n=(6, 5, 4), det=(7, 6), n_views=3, arc=200.0)
+    A_brute = _brute_dense_A(g)
+    got = np.array([[O.clip_ray_voxel(g, r, v) for v in range(g.M)] for r in range(g.N)])
+    assert np.count_nonzero(A_brute > 1e-9) > 100
+    np.testing.assert_allclose(got, A_brute, rtol=0, atol=1e-12)
+
+
 def test_forward_rays_subset():
     g = P.c1_small().geometry
     x = P.random_volume(g, 8)
