@@ -143,6 +143,10 @@ typedef struct {
     double total_ms[PICCS_KERNEL_CLASSES];    /* summed device time per class (only
                                                  while timing is enabled, else 0) */
     long long total_launches;                 /* all kernels of this library */
+    long long calls[PICCS_KERNEL_CLASSES];    /* operator applications per class: one
+                                                 per timed interval of total_ms (a
+                                                 backprojection A^T is one call of two
+                                                 kernels, ray scaling and gather) */
 } piccs_profile;
 
 typedef struct piccs_ctx piccs_ctx;
@@ -286,16 +290,17 @@ int piccs_profile_read(piccs_ctx *ctx, piccs_profile *out);
  * z-fastest FP32 volume (lambda2_piple = lambda^2 for PIPLE, else 0), on
  * cuda_stream (a cudaStream_t; NULL = legacy default stream).  d_omega, d_z,
  * d_out (M floats) and d_rho (one double) are caller-owned device buffers.
- * The paper has no counterpart: this is a deployment variant of the
- * regularisation step of Sec. 2.3.
+ * The paper has no counterpart to this entry point.
  *   Scratch: the per-CTA FP64 partial sums live in a 32 KiB (4096 doubles)
  *   array inside libpiccs that every GPU loading the library holds until
  *   exit; volumes of any size up to 2^31-1 voxels use at most 1216 entries,
  *   larger ones are rejected with PICCS_EINVAL.  Nothing is allocated or
  *   freed (no cudaMalloc, cudaFree or allocating library routine).
  *   The first call on a device looks up the array's device address on that
- *   device (cudaGetSymbolAddress); make that first call before any stream
- *   capture.  All calls share the array and it keeps the last call's
+ *   device (cudaGetSymbolAddress) and keeps it for the life of the process;
+ *   make that first call before any stream capture.  A cudaDeviceReset of
+ *   that device invalidates the kept address: do not call this entry point
+ *   on a device after resetting it.  All calls share the array and it keeps the last call's
  *   contents (every call overwrites what it reads, so nothing needs
  *   clearing); calls whose kernels overlap on the GPU, e.g. from two
  *   streams, race on it and must be serialised by the caller.

@@ -143,6 +143,8 @@ cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const 
 
 // ---- regulariser (kernels_reg.cu) ----
 struct VolDims { int nx, ny, nz; };
+// stencil grids: at most 152 SMs x 8 resident CTAs of 256 threads
+constexpr int kStencilMaxBlocks = 152 * 8;
 int stencil_blocks(long long M);
 cudaError_t launch_weights(VolDims d, const float *x, const float *xp, float alpha2,
                            float lambda2, float tau2, int rule, int variant, float *omega,

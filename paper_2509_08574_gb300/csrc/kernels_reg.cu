@@ -347,7 +347,7 @@ int stencil_blocks(long long M)
 {
     // persistent-style grid: 152 SMs x 8 resident CTAs of 256 threads
     long long want = (M + kThreads - 1) / kThreads;
-    const long long cap = 152LL * 8;
+    const long long cap = kStencilMaxBlocks;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 

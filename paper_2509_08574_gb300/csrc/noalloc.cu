@@ -15,7 +15,10 @@
 // this library holds it (32 KiB) until the process exits.  In host code its
 // name is only a host-side stand-in for the device symbol, so the device
 // address is looked up once per device with cudaGetSymbolAddress (on the first
-// call made with that device current) and passed to the kernels.
+// call made with that device current) and passed to the kernels.  The address
+// is kept for the life of the process, so the entry point must not be used on
+// a device after a cudaDeviceReset of it (the module, and with it the array,
+// may then be loaded at another address).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,6 +31,9 @@ namespace {
 
 constexpr int kScratchDoubles = 4096;  // maximum per-CTA partial sums
 constexpr int kMaxDevices = 64;
+// the stencil grid never exceeds kStencilMaxBlocks CTAs, whatever the volume
+static_assert(piccs::kStencilMaxBlocks <= kScratchDoubles,
+              "the partial-sum scratch must hold one entry per stencil CTA");
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -52,9 +58,7 @@ extern "C" int piccs_reg_normal_noalloc(int nx, int ny, int nz, const float *d_o
     if (!d_omega || !d_z || !d_out || !d_rho) return fail(PICCS_EINVAL, "NULL buffer");
     if (!std::isfinite(lambda2_piple) || lambda2_piple < 0.f)
         return fail(PICCS_EINVAL, "lambda2_piple must be finite and >= 0");
-    const int blocks = piccs::stencil_blocks(M);
-    if (blocks > kScratchDoubles)
-        return fail(PICCS_EINVAL, "volume needs more partial sums than the 4096-entry scratch holds");
+    const int blocks = piccs::stencil_blocks(M);  // <= kStencilMaxBlocks (static_assert above)
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
