@@ -83,10 +83,8 @@ def workload(name="c2_needle"):
     return WORKLOADS[name]()
 
 
-def workload_config(scan, solver="cgls", workspace_bytes=None):
+def workload_config(scan, solver="cgls"):
     g = scan.geometry
-    ws = (f"workspace {workspace_bytes / 1e9:.2f} GB" if workspace_bytes
-          else "working set larger than L2")
     return {
         "workload": (f"{scan.name}: {g.nx}^3 x {g.vx:g} mm volume, {g.n_views} views over "
                      f"{np.degrees((g.angles[1] - g.angles[0]) * g.n_views):.0f} deg, "
@@ -97,9 +95,19 @@ def workload_config(scan, solver="cgls", workspace_bytes=None):
         "volume": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.nu, g.nv],
         "iterations": scan.iterations, "alpha": scan.alpha, "lambda": scan.lam, "tau": scan.tau,
         "projection_layout": "view,u,v (v fastest)",
-        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); {ws}",
+        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); working set larger than L2",
         "parallelism": "replicas (one independent reconstruction per GPU)",
     }
+
+
+def bench_config(scan, args):
+    """The line's config, identical in both arms: the workload plus the run's
+    batch, storage and number of noise draws."""
+    draws = 1 if args.workload in GPU_SYNTH else max(1, args.seeds)
+    return dict(workload_config(scan, args.solver), batch=max(1, args.batch),
+                storage=args.storage, noise_draws=draws,
+                value=("whole-job ms per scan: p50 step time (max over ranks) / "
+                       "(ranks x scans per step); p50_ms/p99_ms: one replica's ms per scan"))
 
 
 def nnz_of(scan):
@@ -227,6 +235,18 @@ class ClockSampler:
         return parse_clock_csv(text)
 
 
+def projector_ms_per_application(prof, batch):
+    """Device ms of one application of A and of A^T per scan, from a library
+    profile: each class's summed time over its operator calls (not its kernel
+    launches -- one A^T is two kernels), divided by the scans one batched call
+    serves."""
+    per = {}
+    for kind in ("forward", "adjoint"):
+        n = prof["calls"][kind]
+        per[kind] = (prof["total_ms"][kind] / n / batch) if n else float("nan")
+    return per
+
+
 def pctl(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
 
@@ -303,7 +323,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(scan, args.solver),
+        "config": bench_config(scan, args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -428,10 +448,7 @@ def run_ours(args):
     # roofline of the dominant kernel (measured live inside the timed region)
     nnz = nnz_of(scan)
     peaks, peak_kind = measured_peaks()
-    per = {}
-    for kind in ("forward", "adjoint"):  # per scan: a batched launch serves B scans
-        n = prof["launches"][kind]
-        per[kind] = (prof["total_ms"][kind] / n / B) if n else float("nan")
+    per = projector_ms_per_application(prof, B)
     dom = max(("forward", "adjoint"), key=lambda k: prof["total_ms"][k])
     nz_ = nnz if nnz is not None else float("nan")  # no exact count: no roofline
     alg_bytes = 4.0 * (nz_ + g.M + g.N)
@@ -447,11 +464,8 @@ def run_ours(args):
         "value": p50 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms * B / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(scan, args.solver,
-                                       pk.piccs_query_workspace_batched(g, params, B)),
-                       batch=B, storage=args.storage, noise_draws=len(inputs),
-                       value=("whole-job ms per scan: p50 step time (max over ranks) / "
-                              "(ranks x scans per step); p50_ms/p99_ms: one replica's ms per scan")),
+        "config": bench_config(scan, args),
+        "workspace_bytes": int(pk.piccs_query_workspace_batched(g, params, B)),
         "p50_ms": p50, "p99_ms": p99,
         "job_scans_per_s": world * args.steps * B / (total_ms * B * 1e-3),
         "e2e": {"value": e2e_p50, "unit": UNIT, "h2d_bytes_per_step": int(B * g.N * 4),
@@ -460,6 +474,7 @@ def run_ours(args):
         "kernel_ms_per_step": {k: v / args.steps for k, v in prof["total_ms"].items()},
         "kernel_ms_per_scan": {k: v / args.steps / B for k, v in prof["total_ms"].items()},
         "launches_per_step": {k: v / args.steps for k, v in prof["launches"].items()},
+        "calls_per_step": {k: v / args.steps for k, v in prof["calls"].items()},
         "projector": {"nnz": nnz, "fwd_ms": per["forward"], "adj_ms": per["adjoint"],
                       "fwd_gups": nz_ / (per["forward"] * 1e-3) / 1e9,
                       "adj_gups": nz_ / (per["adjoint"] * 1e-3) / 1e9},

@@ -88,7 +88,7 @@ KERNEL_CLASSES = ("forward", "adjoint", "reg", "vector", "scalar")
 
 class piccs_profile(C.Structure):
     _fields_ = [("launches", C.c_longlong * 5), ("total_ms", C.c_double * 5),
-                ("total_launches", C.c_longlong)]
+                ("total_launches", C.c_longlong), ("calls", C.c_longlong * 5)]
 
 
 def _load():
@@ -355,6 +355,7 @@ def piccs_profile_read(ctx) -> dict:
     p = piccs_profile()
     _check(_lib.piccs_profile_read(ctx, C.byref(p)), ctx)
     return {"launches": {k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
+            "calls": {k: int(p.calls[i]) for i, k in enumerate(KERNEL_CLASSES)},
             "total_ms": {k: float(p.total_ms[i]) for i, k in enumerate(KERNEL_CLASSES)},
             "total_launches": int(p.total_launches)}
 

@@ -61,13 +61,18 @@ struct piccs_ctx {
     double *dsum = nullptr;
 
     // CUDA graphs of staged reconstructions, by (params, active slots)
-    struct GraphEntry { cudaGraphExec_t exec = nullptr; long long launches[PICCS_KERNEL_CLASSES] = {}; };
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        long long launches[PICCS_KERNEL_CLASSES] = {};
+        long long calls[PICCS_KERNEL_CLASSES] = {};
+    };
     std::map<std::string, GraphEntry> graphs;
     long long graph_launches = 0;
     cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot capture)
     // kernel accounting
     bool timing = false;
     long long launches[PICCS_KERNEL_CLASSES] = {};
+    long long calls[PICCS_KERNEL_CLASSES] = {};
     double total_ms[PICCS_KERNEL_CLASSES] = {};
     struct Pending { int kind; cudaEvent_t a, b; };
     std::vector<Pending> pending;
@@ -111,8 +116,9 @@ cudaEvent_t take_event(piccs_ctx *ctx)
     return e;
 }
 
-// Counts one kernel launch of class `kind` and, with timing on, brackets it
-// with two events on the context's stream.
+// Counts one operator call of class `kind` (its kernel launches and the call
+// itself) and, with timing on, brackets it with two events on the context's
+// stream.
 struct Launch {
     piccs_ctx *ctx;
     int kind;
@@ -121,6 +127,7 @@ struct Launch {
     {
         // the backprojection is two kernels (ray scaling, gather)
         ctx->launches[kind] += kind == PICCS_KERNEL_ADJOINT ? 2 : 1;
+        ctx->calls[kind] += 1;
         if (ctx->timing) {
             a = take_event(ctx);
             if (a) cudaEventRecord(a, ctx->stream);
@@ -448,6 +455,7 @@ int piccs_profile_enable(piccs_ctx *ctx, int timing)
     ctx->pending.clear();
     for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
         ctx->launches[k] = 0;
+        ctx->calls[k] = 0;
         ctx->total_ms[k] = 0.0;
     }
     ctx->timing = timing != 0;
@@ -468,6 +476,7 @@ int piccs_profile_read(piccs_ctx *ctx, piccs_profile *out)
     std::memset(out, 0, sizeof *out);
     for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
         out->launches[k] = ctx->launches[k];
+        out->calls[k] = ctx->calls[k];
         out->total_ms[k] = ctx->total_ms[k];
         out->total_launches += ctx->launches[k];
     }
@@ -939,8 +948,9 @@ int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, in
     key.append(reinterpret_cast<const char *>(&nactive), sizeof nactive);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
-        long long before[PICCS_KERNEL_CLASSES];
+        long long before[PICCS_KERNEL_CLASSES], before_calls[PICCS_KERNEL_CLASSES];
         std::memcpy(before, ctx->launches, sizeof before);
+        std::memcpy(before_calls, ctx->calls, sizeof before_calls);
         if (!ctx->cap_stream)
             CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         // capture on the private stream (nothing runs during a capture), then
@@ -964,12 +974,17 @@ int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, in
         ge.exec = exec;
         for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
             ge.launches[k] = ctx->launches[k] - before[k];
+            ge.calls[k] = ctx->calls[k] - before_calls[k];
             ctx->launches[k] = before[k];  // counted when the graph runs
+            ctx->calls[k] = before_calls[k];
         }
         it = ctx->graphs.emplace(key, ge).first;
     }
     CUDA_TRY(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
-    for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) ctx->launches[k] += it->second.launches[k];
+    for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
+        ctx->launches[k] += it->second.launches[k];
+        ctx->calls[k] += it->second.calls[k];
+    }
     ctx->graph_launches += 1;
     return PICCS_OK;
 }

@@ -128,3 +128,37 @@ def test_serving_patients_are_valid_and_seeded():
         assert g.nx in (128, 256, 384) and 30 <= g.n_views <= 120 and 256 <= g.nu <= 768
         assert 20 <= p["n_outer"] * p["n_inner"] <= 40
         pk.piccs_validate(g, pk.make_params(n_outer=p["n_outer"], n_inner=p["n_inner"]))
+
+
+def test_projector_time_is_per_application_not_per_kernel():
+    """One A^T is two kernels (ray scaling, gather) but one timed call: the
+    per-application time must be the class total over its calls, so that
+    time x applications gives back the class total."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # a 3 x 10 CGLS scan: 31 forward calls, 30 backprojections (60 kernels)
+    prof = {"launches": {"forward": 31, "adjoint": 60},
+            "calls": {"forward": 31, "adjoint": 30},
+            "total_ms": {"forward": 31 * 5.36, "adjoint": 30 * 5.46}}
+    per = bench.projector_ms_per_application(prof, 1)
+    assert abs(per["forward"] - 5.36) < 1e-12
+    assert abs(per["adjoint"] - 5.46) < 1e-12
+    assert abs(per["adjoint"] * prof["calls"]["adjoint"] - prof["total_ms"]["adjoint"]) < 1e-9
+    # a batched call serves B scans
+    per4 = bench.projector_ms_per_application(prof, 4)
+    assert abs(per4["adjoint"] - 5.46 / 4) < 1e-12
+
+
+def test_both_arms_state_the_same_config():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        workload, solver, batch, storage, seeds = "c2_needle", "cgls", 1, "f32", 10
+
+    scan = bench.workload("c2_needle")
+    cfg = bench.bench_config(scan, A)
+    assert cfg == bench.bench_config(scan, A)
+    assert cfg["noise_draws"] == 10 and cfg["batch"] == 1 and cfg["storage"] == "f32"
+    assert "workspace" not in cfg["l2"]
