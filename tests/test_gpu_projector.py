@@ -141,19 +141,34 @@ def c2_volume():
 
 
 @pytest.mark.slow
-def test_forward_c2_sampled_rays(pk, c2_volume):
+def test_forward_c2_sampled_rays(pk, c2_volume, record_property):
     g, x = c2_volume
     with pk.Context(g) as ctx:
         y = ctx.forward(_dev(x)).cpu().numpy().reshape(-1)
     rng = np.random.default_rng(21)
     rays = rng.choice(g.N, 4000, replace=False)
     ref = O.forward_rays(g, x.astype(np.float64), rays)
-    assert rel_l2(y[rays], ref) <= TOL
+    got = y[rays].astype(np.float64)
+    assert rel_l2(got, ref) <= TOL
     hit = ref > 0
     assert hit.sum() > 1000
-    # per ray: FP32 ray coordinates carry ~1e-5 voxel of rounding, so a ray's
-    # error is bounded in absolute terms (grazing chords have tiny values)
-    assert np.max(np.abs(y[rays] - ref)) <= 1e-5 * np.abs(ref).max()
+    # Per ray.  The FP32 walk places every plane crossing with a relative
+    # rounding of ~6e-8 of its distance from the source side of the volume
+    # (<= ~400 mm here), i.e. ~2e-5 mm, so each piece length is off by up to
+    # ~5e-5 mm and a ray of K pieces by ~sqrt(K) x that x mu.  A ray with a
+    # chord of at least 5 % of the largest value sums hundreds of pieces of
+    # comparable mu: its relative error stays below 1e-4.  A grazing ray
+    # crosses few voxels and its value can be tiny, so it is held to the
+    # absolute bound only: 1e-5 of the largest ray value.
+    err = np.abs(got - ref)
+    big = ref >= 0.05 * ref.max()
+    assert big.sum() > 1000
+    relerr = err[big] / ref[big]
+    record_property("per_ray_rel_err_max_nongrazing", float(relerr.max()))
+    record_property("per_ray_rel_err_p99_nongrazing", float(np.percentile(relerr, 99)))
+    record_property("per_ray_abs_err_max_over_max", float(err.max() / ref.max()))
+    assert relerr.max() <= 1e-4, relerr.max()
+    assert err.max() <= 1e-5 * np.abs(ref).max()
 
 
 @pytest.mark.slow

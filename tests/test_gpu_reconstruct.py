@@ -1,7 +1,10 @@
 """Parity of the CUDA IRN-PICCS path (reweighting, regularisation stencil,
 Krylov vector work, the whole reconstruction) with the FP64 oracle, through
 the C ABI.  The volume after a fixed iteration count must match the oracle to
-a relative L2 error <= 1e-3; the per-voxel regularisation terms to <= 1e-5."""
+a relative L2 error <= 1e-3, and so must the reconstruction's update x - x0
+(the part the solver computes: a run started at the prior could otherwise
+get its update ~10 % wrong and still pass on the whole volume); the
+per-voxel regularisation terms match to <= 1e-5."""
 import numpy as np
 import pytest
 
@@ -12,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_X = 1e-3
+TOL_UPD = 1e-3
 TOL_REG = 1e-5
 
 
@@ -48,7 +52,8 @@ VARIANTS = [
 
 
 @pytest.mark.parametrize("name,variant,alpha,lam,n_outer,n_inner,x0", VARIANTS)
-def test_reconstruct_matches_oracle_c1(pk, c1, name, variant, alpha, lam, n_outer, n_inner, x0):
+def test_reconstruct_matches_oracle_c1(pk, c1, name, variant, alpha, lam, n_outer, n_inner, x0,
+                                       record_property):
     scan, b, xp = c1
     g = scan.geometry
     params = pk.make_params(alpha, lam, scan.tau, n_outer, n_inner, x0_mode=x0, variant=variant)
@@ -64,12 +69,16 @@ def test_reconstruct_matches_oracle_c1(pk, c1, name, variant, alpha, lam, n_oute
     ref, _, _ = O.irn(g, b.astype(np.float64), xp.astype(np.float64), x0v, alpha, lam, scan.tau,
                       n_outer, n_inner, variant=variant)
     err = rel_l2(x, ref)
+    upd = rel_l2(x - x0v, ref - x0v)
+    record_property("rel_l2", err)
+    record_property("rel_l2_update", upd)
     assert err <= TOL_X, err
+    assert upd <= TOL_UPD, upd
     # the reconstruction moved away from its start
     assert rel_l2(ref, x0v) > 10 * TOL_X if x0 == 0 else True
 
 
-def test_reconstruct_weight_rule_r2(pk, c1):
+def test_reconstruct_weight_rule_r2(pk, c1, record_property):
     scan, b, xp = c1
     g = scan.geometry
     params = pk.make_params(0.5, 0.5, 0.05, 2, 4, weight_rule=1)
@@ -78,10 +87,13 @@ def test_reconstruct_weight_rule_r2(pk, c1):
         x = ctx.reconstruct(_dev(b), params).cpu().numpy()
     ref, _, _ = O.irn(g, b.astype(np.float64), xp.astype(np.float64), xp.astype(np.float64), 0.5,
                       0.5, 0.05, 2, 4, variant=O.PICCS, rule=O.RULE_R2)
+    upd = rel_l2(x - xp, ref - xp)
+    record_property("rel_l2_update", upd)
     assert rel_l2(x, ref) <= TOL_X
+    assert upd <= TOL_UPD, upd
 
 
-def test_reconstruct_user_x0_and_ragged_sizes(pk):
+def test_reconstruct_user_x0_and_ragged_sizes(pk, record_property):
     g = P.Geometry(13, 11, 9, 1.0, 1.2, 0.9, 21, 37, 1.1, 0.7, 40.0, 65.0,
                    P.scan_angles(11, 360.0, 3.0))
     rng = np.random.default_rng(3)
@@ -95,7 +107,10 @@ def test_reconstruct_user_x0_and_ragged_sizes(pk):
         x = ctx.reconstruct(_dev(b), params, x0=_dev(x0)).cpu().numpy()
     ref, _, _ = O.irn(g, b.astype(np.float64), xp.astype(np.float64), x0.astype(np.float64), 0.3,
                       0.4, 0.02, 3, 3)
+    upd = rel_l2(x - x0, ref - x0)
+    record_property("rel_l2_update", upd)
     assert rel_l2(x, ref) <= TOL_X
+    assert upd <= TOL_UPD, upd
 
 
 def test_reconstruct_host_buffers_match_device(pk, c1):
@@ -188,22 +203,3 @@ def test_nonfinite_prior_and_missing_prior(pk, c1):
         with pytest.raises(pk.PiccsError) as e:
             ctx.reconstruct(_dev(b), pk.make_params())
         assert e.value.code == pk.PICCS_EINVAL
-
-
-@pytest.mark.slow
-def test_reconstruct_c2_first_iterations_match_oracle(pk):
-    """The 256^3 x 90 x 512^2 workload the bench times, one cycle of two CGLS
-    steps, against the FP64 oracle run on the host cores."""
-    scan = P.c2_needle()
-    g = scan.geometry
-    b = scan.measured()
-    xp = P.voxelize(scan.prior_phantom, g, ss=1).astype(np.float32)
-    params = pk.make_params(scan.alpha, scan.lam, scan.tau, 1, 2)
-    with pk.Context(g) as ctx:
-        ctx.set_prior(_dev(xp))
-        x = ctx.reconstruct(_dev(b), params).cpu().numpy()
-        assert ctx.report().status == 0
-    ref, _, _ = O.irn(g, b.astype(np.float64), xp.astype(np.float64), xp.astype(np.float64),
-                      scan.alpha, scan.lam, scan.tau, 1, 2)
-    assert rel_l2(x, ref) <= TOL_X
-    assert rel_l2(x - xp, ref - xp) <= 2e-2
