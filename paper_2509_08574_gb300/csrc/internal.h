@@ -42,6 +42,7 @@ struct ProjGeom {
     float halfnz;           // nz / 2
     float rdv, cv;          // 1 / dv and (nv - 1) / 2: row index of height v = v * rdv + cv
     int sv32;               // sv as a 32-bit stride (1 or nu)
+    int multi;              // a cell can hold more than one z crossing of a row
 };
 
 // Scans of one geometry processed together ("slots", Sec. 3's repeated scans

@@ -103,7 +103,73 @@ __device__ __forceinline__ void decode_block(const ProjGeom &G, int &col, int &p
     p = ((b - col * nrgb) * kRowGroups + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
 }
 
-template <int MODE, bool NORM>
+// Walk of one mirror pair of rows (heights v >= 0 and -v) along the
+// column's cell list; acca / accb get the upper / lower ray's sum of
+// piece length (xy mm) x voxel value.  Every lane takes one piece per cell,
+// [s, min(next crossing, se)] in its current layer, with its length clamped
+// at 0 so that a ray that has left the volume (or never entered it) adds
+// exactly nothing; the z crossings inside a cell are then taken as one
+// warp-uniform step, predicated per lane, and only when some lane crosses.
+// When the host has shown that a cell holds at most one crossing of any row
+// (the xy distance between consecutive z planes of the steepest ray, vz D /
+// v_max, exceeds the longest cell), one such step per cell suffices; MULTI
+// repeats it until no lane crosses any more.  The piece lengths are the
+// expressions the adjoint's gather evaluates, bit for bit.
+template <bool MULTI>
+__device__ __forceinline__ void walk_pair(const ProjGeom &G, const ColParams &cp,
+                                          const int4 *__restrict__ cells,
+                                          const float *__restrict__ vol, float2 w, bool pair_ok,
+                                          float &acca, float &accb)
+{
+    const float inv = cp.KD * w.y;  // xy distance per voxel of z (> 0)
+    const int nzm1 = G.nz - 1;
+    int iz = __float2int_rd(w.x * (cp.s0 * cp.rKD) + G.halfnz);
+    const bool act = pair_ok && iz >= 0 && iz < G.nz;
+    // centred coordinate of the plane the upper ray leaves layer iz through,
+    // and the xy distance at which it does; the FP32 layer index can disagree
+    // with the sign of a tiny z offset: a first crossing "behind" the entry
+    // is taken at the entry
+    float kce = (float)(iz + 1) - G.halfnz;
+    float szn = fmaxf(fmaf(kce, inv, -cp.s0), 0.f);
+    if (!act) {  // in the top layer with its "exit" behind it: adds 0, never crosses
+        iz = nzm1;
+        szn = -1.f;
+    }
+    if (!__any_sync(kFull, act)) return;
+    const int4 *t = cells + cp.start2;
+    const int n2 = (cp.ncells + 1) >> 1;
+    float s = 0.f;
+    auto cell = [&](int colbase, float se) {
+        const float *cpv = vol + colbase;
+        const float len = fmaxf(fminf(szn, se) - s, 0.f);
+        acca = fmaf(len, __ldg(cpv + iz), acca);
+        accb = fmaf(len, __ldg(cpv + (nzm1 - iz)), accb);
+        do {
+            const bool up = szn < se && iz < nzm1;
+            if (!__any_sync(kFull, up)) break;
+            const float kn = kce + 1.f;
+            const float sn = fmaf(kn, inv, -cp.s0);
+            const float l2 = up ? fminf(sn, se) - szn : 0.f;
+            if (up) {
+                ++iz;
+                kce = kn;
+                szn = sn;
+            }
+            acca = fmaf(l2, __ldg(cpv + iz), acca);
+            accb = fmaf(l2, __ldg(cpv + (nzm1 - iz)), accb);
+        } while (MULTI);
+        s = se;
+    };
+    for (int c = 0; c < n2; ++c) {
+        const int4 e = __ldg(t + c);
+        cell(e.x, __int_as_float(e.y));
+        cell(e.z, __int_as_float(e.w));
+        // every lane has left the volume through a z face
+        if ((c & 1) && !__any_sync(kFull, iz < nzm1 || szn >= s)) break;
+    }
+}
+
+template <int MODE, bool NORM, bool MULTI>
 __global__ void __launch_bounds__(256)
 fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
            const int4 *__restrict__ cells, const float *__restrict__ vol,
@@ -131,47 +197,8 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
     const ColParams cp = cols[col];
     if (cp.ncells > 0) {
         const float2 w = pair_ok ? __ldg(vr + iva) : make_float2(0.f, 1e30f);
-        const float inv = cp.KD * w.y;          // xy distance per voxel of z (> 0)
         sec = ray_sec(w.x, cp.invD);
-        const int nzm1 = G.nz - 1;
-        int iz = __float2int_rd(w.x * (cp.s0 * cp.rKD) + G.halfnz);
-        bool act = pair_ok && iz >= 0 && iz < G.nz;
-        if (!act) iz = 0;
-        // centred coordinate of the plane the upper ray leaves layer iz through
-        float kce = (float)(iz + 1) - G.halfnz;
-        // the FP32 layer index can disagree with the sign of a tiny z offset:
-        // a first crossing "behind" the entry is taken at the entry
-        float szn = fmaxf(fmaf(kce, inv, -cp.s0), 0.f);
-        if (__any_sync(kFull, act)) {
-            const int4 *t = cells + cp.start2;
-            const int n2 = (cp.ncells + 1) >> 1;
-            float s = 0.f;
-            // one xy cell [s, se] of the voxel column at colbase: the pair's pieces
-            auto cell = [&](int colbase, float se) {
-                const float *cpv = vol + colbase;
-                if (act) {
-                    float len = fminf(szn, se) - s;
-                    acca = fmaf(len, __ldg(cpv + iz), acca);
-                    accb = fmaf(len, __ldg(cpv + (nzm1 - iz)), accb);
-                    while (szn < se) {
-                        const float sl = szn;
-                        if (++iz >= G.nz) { act = false; break; }
-                        kce += 1.f;
-                        szn = fmaf(kce, inv, -cp.s0);
-                        len = fminf(szn, se) - sl;
-                        acca = fmaf(len, __ldg(cpv + iz), acca);
-                        accb = fmaf(len, __ldg(cpv + (nzm1 - iz)), accb);
-                    }
-                }
-                s = se;
-            };
-            for (int c = 0; c < n2; ++c) {
-                const int4 e = __ldg(t + c);
-                cell(e.x, __int_as_float(e.y));
-                cell(e.z, __int_as_float(e.w));
-                if ((c & 1) && !__any_sync(kFull, act)) break;
-            }
-        }
+        walk_pair<MULTI>(G, cp, cells, vol, w, pair_ok, acca, accb);
     }
 
     float sq = 0.f;
@@ -385,9 +412,17 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
     const int nb = project_blocks(g);
     if (nb <= 0 || sl.n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)nb, (unsigned)sl.n);
-#define PICCS_FWD(M, NORM) \
-    fwd_kernel<M, NORM><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, partials, \
-                                              nonfinite, nullptr, nullptr, sl.stride)
+#define PICCS_FWD(M, NORM)                                                                   \
+    do {                                                                                     \
+        if (g.multi)                                                                         \
+            fwd_kernel<M, NORM, true><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, \
+                                                            partials, nonfinite, nullptr,     \
+                                                            nullptr, sl.stride);              \
+        else                                                                                 \
+            fwd_kernel<M, NORM, false><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, out, aux, \
+                                                             partials, nonfinite, nullptr,     \
+                                                             nullptr, sl.stride);              \
+    } while (0)
     if (mode == FWD_RESID) {
         if (partials) PICCS_FWD(FWD_RESID, true); else PICCS_FWD(FWD_RESID, false);
     } else if (mode == FWD_RESID16) {
@@ -406,8 +441,14 @@ cudaError_t launch_forward_lsqr(const ProjGeom &g, const ColParams *cols, const 
     const int nb = project_blocks(g);
     if (nb <= 0 || sl.n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)nb, (unsigned)sl.n);
-    fwd_kernel<FWD_LSQR, true><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux, partials,
-                                                     nullptr, rA, Aw, sl.stride);
+    if (g.multi)
+        fwd_kernel<FWD_LSQR, true, true><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux,
+                                                               partials, nullptr, rA, Aw,
+                                                               sl.stride);
+    else
+        fwd_kernel<FWD_LSQR, true, false><<<grid, 256, 0, st>>>(g, cols, vr, cells, vol, U, aux,
+                                                                partials, nullptr, rA, Aw,
+                                                                sl.stride);
     return cudaGetLastError();
 }
 

@@ -362,6 +362,17 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
     ctx->pg.rdv = (float)(1.0 / g.dv);
     ctx->pg.cv = 0.5f * (float)(g.nv - 1);
     ctx->pg.sv32 = (int)ctx->pg.sv;
+    {
+        // Consecutive z planes lie vz D / |v| apart in xy distance along a row
+        // of height v (D >= DSD the source-to-pixel xy distance); if that
+        // exceeds the longest xy cell (the voxel's diagonal) for the steepest
+        // row, with a margin far above FP32 rounding, no cell holds two
+        // crossings of a row and the forward walk takes one crossing step per
+        // cell.
+        const double vmax = 0.5 * (g.nv - 1) * g.dv;
+        const double diag = std::sqrt(g.vx * g.vx + g.vy * g.vy);
+        ctx->pg.multi = vmax > 0.0 && g.vz * g.dsd <= 1.01 * diag * vmax ? 1 : 0;
+    }
     ctx->vd = VolDims{g.nx, g.ny, g.nz};
 
     e = cudaMalloc(&ctx->base, L.total);

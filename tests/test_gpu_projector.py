@@ -60,6 +60,10 @@ GEOMS = {
     # detector much wider than the volume: many rays miss, some graze
     "misses": lambda: P.Geometry(24, 20, 16, 0.5, 0.5, 0.5, 64, 48, 1.0, 1.0, 60.0, 100.0,
                                  P.scan_angles(5, 360.0, 11.0), P.LAYOUT_VU),
+    # thin z voxels under a wide cone: rows steeper than 2 mm at the detector
+    # cross several z planes inside one xy cell (the walk's multi-crossing path)
+    "multi_crossing": lambda: P.Geometry(8, 8, 60, 2.0, 2.0, 0.1, 16, 24, 1.5, 0.5, 40.0, 60.0,
+                                         P.scan_angles(5, 360.0, 2.0)),
     # truncated: detector smaller than the volume shadow, anisotropic voxels
     "truncated": lambda: P.Geometry(40, 36, 32, 0.8, 0.9, 0.6, 24, 40, 0.8, 0.5, 120.0, 180.0,
                                     P.scan_angles(9, 200.0, 5.0)),
