@@ -43,6 +43,7 @@ struct ProjGeom {
     float rdv, cv;          // 1 / dv and (nv - 1) / 2: row index of height v = v * rdv + cv
     int sv32;               // sv as a 32-bit stride (1 or nu)
     int multi;              // a cell can hold more than one z crossing of a row
+    float rows_per_layer;   // detector rows one voxel layer spans at the isocentre
 };
 
 // Scans of one geometry processed together ("slots", Sec. 3's repeated scans
@@ -123,9 +124,13 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
                            const int4 *cells, const float *vol, float *out, int mode,
                            const float *aux, double *partials, int *nonfinite, cudaStream_t st,
                            Slots sl = Slots{1, 0});
-// vol += A^T proj (vol holds the starting values, e.g. zeros); rs is an
-// N-float scratch that receives proj scaled by each ray's sec (rounded to
-// BF16, N of them, when rs_bf16).
+// vol += A^T proj (vol holds the starting values, e.g. zeros); rs is a
+// scratch of adjoint_rs_floats(g) floats: per detector column the prefix sums
+// of proj scaled by each ray's sec (adjoint_uses_prefix), else those scaled
+// values themselves (in BF16, N of them, when rs_bf16).  rs_bf16 rounds each
+// scaled value to BF16 before it is summed.
+bool adjoint_uses_prefix(const ProjGeom &g);
+inline long long adjoint_rs_floats(long long N, long long ncol) { return N + 2 * ncol; }
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
                            float *vol, cudaStream_t st, Slots sl = Slots{1, 0},

@@ -234,7 +234,7 @@ Layout plan(const piccs_geometry *g, int nslot = 1)
     L.off_r = q; q += align256(N * sizeof(float));
     L.off_q = q; q += align256(N * sizeof(float));
     L.off_b = q; q += align256(N * sizeof(float));
-    L.off_rs = q; q += align256(N * sizeof(float));
+    L.off_rs = q; q += align256((size_t)adjoint_rs_floats((long long)N, (long long)g->n_views * g->nu) * sizeof(float));
     L.off_aw = q; q += align256(N * sizeof(float));
     L.off_pf = q; q += align256((size_t)L.n_pf * sizeof(double));
     L.off_pv = q; q += align256(3 * (size_t)L.n_pv * sizeof(double));  // up to 3 sums per pass
@@ -372,6 +372,7 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
         const double vmax = 0.5 * (g.nv - 1) * g.dv;
         const double diag = std::sqrt(g.vx * g.vx + g.vy * g.vy);
         ctx->pg.multi = vmax > 0.0 && g.vz * g.dsd <= 1.01 * diag * vmax ? 1 : 0;
+        ctx->pg.rows_per_layer = (float)(g.vz * g.dsd / (g.dso * g.dv));
     }
     ctx->vd = VolDims{g.nx, g.ny, g.nz};
 

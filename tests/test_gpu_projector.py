@@ -64,6 +64,14 @@ GEOMS = {
     # cross several z planes inside one xy cell (the walk's multi-crossing path)
     "multi_crossing": lambda: P.Geometry(8, 8, 60, 2.0, 2.0, 0.1, 16, 24, 1.5, 0.5, 40.0, 60.0,
                                          P.scan_angles(5, 360.0, 2.0)),
+    # even sizes and a dense detector (2.7 rows per voxel layer): the
+    # prefix-sum adjoint, 35 upper layers, two per lane and one in the last lane
+    "prefix_partial_lane": lambda: P.Geometry(20, 18, 70, 1.0, 1.0, 0.5, 30, 120, 1.2, 0.3, 100.0,
+                                              160.0, P.scan_angles(5, 200.0, 3.0)),
+    # the prefix-sum adjoint with one layer per lane (20 upper layers),
+    # 3.75 rows per layer, some rays leaving through the top and bottom faces
+    "prefix_dense_rows": lambda: P.Geometry(24, 22, 40, 1.0, 1.0, 1.0, 32, 96, 1.0, 0.4, 100.0,
+                                            150.0, P.scan_angles(6, 360.0, 1.0)),
     # truncated: detector smaller than the volume shadow, anisotropic voxels
     "truncated": lambda: P.Geometry(40, 36, 32, 0.8, 0.9, 0.6, 24, 40, 0.8, 0.5, 120.0, 180.0,
                                     P.scan_angles(9, 200.0, 5.0)),
