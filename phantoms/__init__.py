@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -382,13 +383,20 @@ class Scan:
     tau: float
     n_outer: int
     n_inner: int
+    prior_file: Optional[str] = None  # stored prior volume (float32 .npy), if any
 
     @property
     def iterations(self) -> int:
         return self.n_outer * self.n_inner
 
     def prior_volume(self, ss: int = 2) -> np.ndarray:
-        """Prior x_p: voxelised change-free phantom (float32)."""
+        """Prior x_p (float32): the stored fixture when the workload has one
+        (a reconstruction from a dense scan of the change-free phantom), else
+        the change-free phantom voxelised on an ss^3 sub-grid."""
+        if self.prior_file is not None:
+            x = np.load(self.prior_file)
+            assert x.shape == self.geometry.vol_shape() and x.dtype == np.float32
+            return x
         return voxelize(self.prior_phantom, self.geometry, ss).astype(np.float32)
 
     def truth_volume(self, ss: int = 2) -> np.ndarray:
@@ -400,10 +408,16 @@ class Scan:
         return poisson_log_data(li, self.I0, self.noise_seed).astype(np.float32)
 
 
+_GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests",
+                       "golden")
+
+
 def c1_small(layout: int = LAYOUT_UV) -> Scan:
     """64^3 x 1 mm, 40 views / 360 deg, 96x96 x 1.2 mm, DSO 1000, DSD 1500,
     additive seeded ellipsoid head (water-like 0.02/mm body) plus a sphere
-    of radius 4 voxels (0.025/mm), I0 = 1e5, alpha 0.5, 15 iterations."""
+    of radius 4 voxels (0.025/mm), I0 = 1e5, alpha 0.5, 15 iterations.  The
+    prior is the change-free head reconstructed from 360 views (20 plain CGLS
+    iterations in the FP64 oracle; tests/golden/make_c1_prior.py)."""
     g = Geometry(64, 64, 64, 1.0, 1.0, 1.0, 96, 96, 1.2, 1.2, 1000.0, 1500.0,
                  scan_angles(40, 360.0), layout)
     prior = ellipsoid_phantom(g, 10, seed=1, mu_lo=-0.004, mu_hi=0.006,
@@ -412,7 +426,7 @@ def c1_small(layout: int = LAYOUT_UV) -> Scan:
     c = np.array([rng.uniform(-10, 10), rng.uniform(-10, 10), rng.uniform(-8, 8)])
     sphere = Ellipsoid(c, np.full(3, 4.0), np.eye(3), 0.005)
     return Scan("c1_64cubed_40views", g, prior, prior + [sphere], 1e5, 11,
-                0.5, 0.5, 1e-2, 3, 5)
+                0.5, 0.5, 1e-2, 3, 5, os.path.join(_GOLDEN, "c1_prior_360views.npy"))
 
 
 def c2_needle(layout: int = LAYOUT_UV) -> Scan:
