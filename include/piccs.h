@@ -87,8 +87,7 @@ enum { PICCS_X0_PRIOR = 0, PICCS_X0_ZERO = 1, PICCS_X0_USER = 2 };
 enum { PICCS_SOLVER_CGLS = 0, PICCS_SOLVER_LSQR = 1, PICCS_SOLVER_LSQR_REORTH = 2 };
 
 /* Storage precision.  F32: every vector in FP32.  BF16: the measured
- * projections b, the backprojection's per-ray values (the residual scaled by
- * the ray's secant) and the LSQR re-orthogonalisation basis are held in BF16
+ * projections b and the LSQR re-orthogonalisation basis are held in BF16
  * (rounded to nearest even once, when stored); rays still accumulate in FP32,
  * the recurrence vectors (residuals, search directions, iterates) stay FP32
  * and every inner product and Krylov scalar is FP64.  FP32 input is rounded

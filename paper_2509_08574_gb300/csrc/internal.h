@@ -125,16 +125,14 @@ cudaError_t launch_forward(const ProjGeom &g, const ColParams *cols, const float
                            const float *aux, double *partials, int *nonfinite, cudaStream_t st,
                            Slots sl = Slots{1, 0});
 // vol += A^T proj (vol holds the starting values, e.g. zeros); rs is a
-// scratch of adjoint_rs_floats(g) floats: per detector column the prefix sums
-// of proj scaled by each ray's sec (adjoint_uses_prefix), else those scaled
-// values themselves (in BF16, N of them, when rs_bf16).  rs_bf16 rounds each
-// scaled value to BF16 before it is summed.
+// scratch of adjoint_rs_floats(N, views x columns) floats: per detector
+// column the prefix sums of proj scaled by each ray's sec
+// (adjoint_uses_prefix), else those N scaled values themselves.
 bool adjoint_uses_prefix(const ProjGeom &g);
 inline long long adjoint_rs_floats(long long N, long long ncol) { return N + 2 * ncol; }
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st, Slots sl = Slots{1, 0},
-                           bool rs_bf16 = false);
+                           float *vol, cudaStream_t st, Slots sl = Slots{1, 0});
 // n FP32 values per slot -> BF16 (round to nearest even)
 cudaError_t launch_to_bf16(long long n, const float *src, long long src_stride, void *dst,
                            long long dst_stride, int nslot, cudaStream_t st);

@@ -68,11 +68,6 @@ __device__ __forceinline__ float ray_sec(float v, float invD)
     return __fsqrt_rn(fmaf(m, m, 1.f));
 }
 
-// ray values are FP32, or BF16 when the context stores projections in BF16
-__device__ __forceinline__ float ld_ray(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_ray(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-__device__ __forceinline__ void st_ray(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st_ray(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -170,8 +165,10 @@ __device__ __forceinline__ void walk_pair(const ProjGeom &G, const ColParams &cp
     }
 }
 
+// 8 CTAs of 256 threads per SM (32 registers): the walk's gathers need the
+// full occupancy to hide their latency once the volume no longer fits in L2
 template <int MODE, bool NORM, bool MULTI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)
 fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
            const int4 *__restrict__ cells, const float *__restrict__ vol,
            float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
@@ -189,6 +186,12 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         aw = slot_ptr(aw, so);
     }
     if (MODE == FWD_LSQR && aux[2] != 0.f) return;  // the Krylov cycle has stopped
+    __shared__ double red[kRowGroups];  // NORM: the warps' partial sums
+    __shared__ unsigned warps_done;
+    if (NORM) {
+        if (threadIdx.x == 0) warps_done = 0;
+        __syncthreads();  // before any warp can finish
+    }
     int col, p;
     decode_block(G, col, p);
     const bool pair_ok = p < npairs_rows(G.nv);
@@ -252,25 +255,37 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         sq = qa * qa + (has_b ? qb * qb : 0.f);
     }
     if (NORM) {
-        __shared__ double red[kRowGroups];
+        // The warps of a CTA finish their walks at different times (steep rows
+        // leave through a z face early).  Instead of a barrier, each warp leaves
+        // its partial in shared memory and the last one to finish sums the
+        // eight in warp order: the same sum, and no warp waits for the slowest
+        // (a barrier here cost 22 % at 512^3, where the gathers miss L2).
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)sq;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = (double)sq;
+            __threadfence_block();
+            if (atomicAdd(&warps_done, 1u) == kRowGroups - 1) {
+                __threadfence_block();
+                const volatile double *rv = red;
+                double t = 0.0;
 #pragma unroll
-            for (int w = 0; w < kRowGroups; ++w) t += red[w];
-            partials[blockIdx.x] = t;
+                for (int w = 0; w < kRowGroups; ++w) t += rv[w];
+                partials[blockIdx.x] = t;
+            }
         }
     }
 }
 
-// rs = proj * sec, per ray (the adjoint's gather then needs no square root)
-template <class RT>
+// rs = proj * sec, per ray (the adjoint's gather then needs no square root).
+// PAIRS (even nv): stored per detector column as mirror-row pairs,
+// rs2[col h + m] = {rs of row h + m, rs of row h - 1 - m} (h = nv / 2), so that
+// the gather fetches a row and its mirror with one 8-byte load; else in the
+// projection layout.
+template <bool PAIRS>
 __global__ void __launch_bounds__(256)
 scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-                  const float *__restrict__ proj, RT *__restrict__ rs, long long sstride)
+                  const float *__restrict__ proj, float *__restrict__ rs, long long sstride)
 {
     proj = slot_ptr(proj, blockIdx.y * sstride);
     rs = slot_ptr(rs, blockIdx.y * sstride);
@@ -282,8 +297,14 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
     const int iva = G.nv - 1 - p;
     const float sec = ray_sec(__ldg(vr + iva).x, cols[col].invD);  // same for the mirror row
     const long long ia = base + (long long)iva * G.sv, ib = base + (long long)p * G.sv;
-    st_ray(rs + ia, proj[ia] * sec);
-    if (p != iva) st_ray(rs + ib, proj[ib] * sec);
+    if (PAIRS) {
+        const int h = G.nv >> 1;
+        reinterpret_cast<float2 *>(rs)[(long long)col * h + (h - 1 - p)] =
+            make_float2(proj[ia] * sec, proj[ib] * sec);
+    } else {
+        rs[ia] = proj[ia] * sec;
+        if (p != iva) rs[ib] = proj[ib] * sec;
+    }
 }
 
 // Adjoint gather: CTA = one xy voxel column (ix, iy), thread = kLayersPerThread
@@ -294,11 +315,14 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // v in [zl, zh] / ((s0 + s) rKD)); each candidate row r is checked with the
 // exact piece length -- the expression the forward walk evaluates -- which is
 // also the length of row nv-1-r in layer p.
-template <class RT>
+// EVEN (even nv and nz): no row has v = 0 and no layer straddles z = 0, so
+// every upper layer is crossed by the upper rows only (iv >= nv / 2), upwards;
+// the ray values are read as mirror-row pairs (scale_rays_kernel<true>).
+template <bool EVEN>
 __global__ void __launch_bounds__(kGatherThreads, PICCS_GATHER_MIN_CTAS)
 adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
-                  const RT *__restrict__ rs, float *__restrict__ vol, long long sstride)
+                  const float *__restrict__ rs, float *__restrict__ vol, long long sstride)
 {
     rs = slot_ptr(rs, blockIdx.z * sstride);
     vol = slot_ptr(vol, blockIdx.z * sstride);
@@ -333,7 +357,8 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             const float s0 = cz.x, KD = cz.y, rKD = cz.w;
             // candidate bounds only: the rows are then checked exactly
             const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
-            const int roff = (int)((long long)j * G.sj + (long long)iu * G.su);  // N < 2^31
+            const int roff = EVEN ? (j * G.nu + iu) * (G.nv >> 1)  // pair index of row nv / 2
+                                  : (int)((long long)j * G.sj + (long long)iu * G.su);  // N < 2^31
             hc_a[threadIdx.x] = make_float4(sa, sb, s0, KD);
             hc_b[threadIdx.x] = make_float4(rGa, rGb, __int_as_float(roff), 0.f);
         }
@@ -342,8 +367,10 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             const float4 ca = hc_a[k], cb = hc_b[k];
             const float sa = ca.x, sb = ca.y, s0 = ca.z, KD = ca.w;
             const float rGa = cb.x, rGb = cb.y;
-            const RT *rsc = rs + __float_as_int(cb.z);
-            const RT *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
+            const float *rsc = rs + __float_as_int(cb.z);
+            const float *rsm = rsc + nvm1 * G.sv32;  // row nv-1-iv at rsm - iv * sv
+            // EVEN: pair of rows iv and nv-1-iv at rp[iv]
+            const float2 *rp = reinterpret_cast<const float2 *>(rs) + __float_as_int(cb.z) - (G.nv >> 1);
 #pragma unroll
             for (int q = 0; q < L; ++q) {
                 const float zl = zlo[q], zh = zl + 1.f;
@@ -352,7 +379,7 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                 const float vlo = zl * (zl >= 0.f ? rGb : rGa), vhi = zh * rGa;
                 int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
                 int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
-                ilo = max(ilo, 0);
+                ilo = max(ilo, EVEN ? (G.nv >> 1) : 0);
                 ihi = pok[q] ? min(ihi, nvm1) : -1;
                 // only a layer touching z = 0 can hold the middle row of an odd nv
                 // (v = 0), which is its own mirror and belongs to the upper layer
@@ -369,9 +396,15 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                                               ? fminf(sb, xh) - fmaxf(sa, xl)
                                               : fminf(sb, fmaxf(xl, xh)) - fmaxf(sa, fminf(xl, xh));
                         if (len > 0.f) {
-                            accu[q] = fmaf(len, ld_ray(rsc + iv * G.sv32), accu[q]);
-                            if (!mid || 2 * iv != nvm1)
-                                accd[q] = fmaf(len, ld_ray(rsm - iv * G.sv32), accd[q]);
+                            if (EVEN) {
+                                const float2 r2 = __ldg(rp + iv);
+                                accu[q] = fmaf(len, r2.x, accu[q]);
+                                accd[q] = fmaf(len, r2.y, accd[q]);
+                            } else {
+                                accu[q] = fmaf(len, __ldg(rsc + iv * G.sv32), accu[q]);
+                                if (!mid || 2 * iv != nvm1)
+                                    accd[q] = fmaf(len, __ldg(rsm - iv * G.sv32), accd[q]);
+                            }
                         }
                     };
                     if (ilo <= ihi) cand(ilo);
@@ -379,7 +412,7 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
                     if (ilo + 2 <= ihi) cand(ilo + 2);
                     for (int iv = ilo + 3; iv <= ihi; ++iv) cand(iv);
                 };
-                if (zl >= 0.f)
+                if (EVEN || zl >= 0.f)
                     rows(std::true_type{});
                 else
                     rows(std::false_type{});
@@ -421,12 +454,10 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // Prefix sums: per detector column, over the upper rows h .. nv-1 (h = nv/2,
 // heights v > 0) counted outwards from the middle, with the mirror row
 // nv-1-i beside row i: pq[c (h + 1) + m] = {sum_{i<h+m} rs_i, sum of the
-// mirror rows}, rs = r sec gamma (rounded to BF16 first when the context
-// keeps its ray values in BF16).  Starting at the middle keeps the sums as
+// mirror rows}, rs = r sec gamma.  Starting at the middle keeps the sums as
 // small as half a column.
 
 // one warp per detector column, 32 rows per step
-template <bool ROUND16>
 __global__ void __launch_bounds__(256)
 ray_prefix_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
                   const float *__restrict__ proj, float2 *__restrict__ pq, long long sstride)
@@ -450,10 +481,6 @@ ray_prefix_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             const float sec = ray_sec(__ldg(vr + iv).x, invD);
             ru = proj[base + (long long)iv * G.sv] * sec;
             rd = proj[base + (long long)(G.nv - 1 - iv) * G.sv] * sec;
-            if (ROUND16) {
-                ru = __bfloat162float(__float2bfloat16_rn(ru));
-                rd = __bfloat162float(__float2bfloat16_rn(rd));
-            }
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {  // inclusive scan over the lanes
@@ -694,7 +721,7 @@ bool adjoint_uses_prefix(const ProjGeom &g)
 
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
-                           float *vol, cudaStream_t st, Slots sl, bool rs_bf16)
+                           float *vol, cudaStream_t st, Slots sl)
 {
     const int nb = project_blocks(g);
     if (nb <= 0 || sl.n <= 0) return cudaSuccess;
@@ -702,10 +729,7 @@ cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float
         const long long ncol = (long long)g.n_views * g.nu;
         const dim3 pgrid((unsigned)((ncol * 32 + 255) / 256), (unsigned)sl.n);
         float2 *pq = reinterpret_cast<float2 *>(rs);
-        if (rs_bf16)
-            ray_prefix_kernel<true><<<pgrid, 256, 0, st>>>(g, cols, vr, proj, pq, sl.stride);
-        else
-            ray_prefix_kernel<false><<<pgrid, 256, 0, st>>>(g, cols, vr, proj, pq, sl.stride);
+        ray_prefix_kernel<<<pgrid, 256, 0, st>>>(g, cols, vr, proj, pq, sl.stride);
         const int hz = g.nz >> 1;
         const int R = (hz + 31) / 32;  // layers per lane: 1 .. kPrefixMaxR
         const dim3 grid((unsigned)((g.nx * g.ny + kPrefixWarps - 1) / kPrefixWarps), (unsigned)sl.n);
@@ -727,15 +751,14 @@ cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float
     const dim3 grid((unsigned)(g.nx * g.ny), (unsigned)((nlp + per_cta - 1) / per_cta),
                     (unsigned)sl.n);
     const dim3 sgrid((unsigned)nb, (unsigned)sl.n);
-    if (rs_bf16) {
-        __nv_bfloat16 *r16 = reinterpret_cast<__nv_bfloat16 *>(rs);
-        scale_rays_kernel<__nv_bfloat16><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, r16, sl.stride);
-        adj_gather_kernel<__nv_bfloat16><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits,
-                                                                         r16, vol, sl.stride);
+    if ((g.nv & 1) == 0 && (g.nz & 1) == 0) {
+        scale_rays_kernel<true><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, rs, sl.stride);
+        adj_gather_kernel<true><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs, vol,
+                                                                 sl.stride);
     } else {
-        scale_rays_kernel<float><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, rs, sl.stride);
-        adj_gather_kernel<float><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs,
-                                                                 vol, sl.stride);
+        scale_rays_kernel<false><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, rs, sl.stride);
+        adj_gather_kernel<false><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs,
+                                                                  vol, sl.stride);
     }
     return cudaGetLastError();
 }

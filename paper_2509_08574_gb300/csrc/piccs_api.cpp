@@ -664,7 +664,7 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
                                                                ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
     // alpha_1 v_1 = A~^T u_1
     LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
-                                                     ctx->rs, ctx->s, st, SL(ctx), bf16));
+                                                     ctx->rs, ctx->s, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr, ls,
                                                     ctx->part_vec, st, SL(ctx)));
     LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
@@ -683,7 +683,7 @@ static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_para
         // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
         if (!last)
             LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
-                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
+                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
         const long long ldb = lsqr_basis_stride(M);
         void *bv = (reorth && !last)
                        ? static_cast<char *>(ctx->basis) + (size_t)(i - 1) * ldb * (bf16 ? 2 : sizeof(float))
@@ -758,7 +758,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
         if (k == 0) {
             LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
                                              ctx->s, 1, nullptr, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st, SL(ctx)));
         } else {
@@ -778,7 +778,7 @@ static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_par
             // after the reconstruction's last step s = A^T r + g only feeds the
             // history, so its backprojection is skipped
             if (k == p->n_outer - 1 && it == p->n_inner - 1) break;
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx), bf16));
+            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
             LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st, SL(ctx)));
         }

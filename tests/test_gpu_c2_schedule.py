@@ -7,11 +7,11 @@ inside the compared run.  Against the FP64 oracle run on the host cores:
 
 * FP32 storage, CGLS and LSQR: the volume and the update x - x_p each
   within rel-L2 1e-3 of the oracle's (same solver);
-* BF16 storage of projections and backprojected ray values (CGLS) and also
-  of the basis (re-orthogonalised LSQR; in exact arithmetic the same
-  iterates as CGLS): the volume within 5e-3 of the oracle's CGLS on the
-  BF16-rounded data and on the exact data, the update within 5e-3 of the
-  former, and the image error to the ground truth within 1 % of the oracle's.
+* BF16 storage of the projections (CGLS) and also of the basis
+  (re-orthogonalised LSQR; in exact arithmetic the same iterates as CGLS):
+  the volume and the update within 1e-3 of the oracle's CGLS on the
+  BF16-rounded data, the volume within 5e-3 of it on the exact data, and
+  the image error to the ground truth within 1 % of the oracle's.
 """
 import numpy as np
 import pytest
@@ -25,8 +25,8 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 N_OUTER, N_INNER = 2, 3
 TOL_X = 1e-3
 TOL_UPD = 1e-3
-TOL_BF16 = 5e-3
-TOL_BF16_UPD = 5e-3
+TOL_BF16_DATA = 1e-3  # against the oracle on the BF16-rounded projections
+TOL_BF16 = 5e-3       # against the oracle on the exact projections
 
 
 @pytest.fixture(scope="module")
@@ -120,9 +120,9 @@ def test_c2_bf16_against_oracle_and_truth(pk, c2, ref_cgls, ref16_cgls, solver, 
     record_property("rel_l2_vs_oracle_bf16_data", e16)
     record_property("rel_l2_vs_oracle_exact_data", e32)
     record_property("rel_l2_update_vs_oracle_bf16_data", upd)
-    assert e16 <= TOL_BF16, e16
+    assert e16 <= TOL_BF16_DATA, e16
+    assert upd <= TOL_BF16_DATA, upd
     assert e32 <= TOL_BF16, e32
-    assert upd <= TOL_BF16_UPD, upd
     truth = P.voxelize(scan.scan_phantom, scan.geometry, ss=1)
     t64, t16 = rel_l2(ref_cgls, truth), rel_l2(x, truth)
     record_property("rel_l2_to_truth_oracle", t64)

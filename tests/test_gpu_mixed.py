@@ -1,16 +1,16 @@
-"""Mixed precision (BF16 storage of the projections, the backprojection's ray
-values and the LSQR basis; FP32 ray accumulation; FP64 inner products and
-Krylov scalars), each result stated against the FP64 oracle:
+"""Mixed precision (BF16 storage of the projections and of the LSQR basis;
+FP32 ray accumulation; FP64 inner products and Krylov scalars), each result
+stated against the FP64 oracle:
 
 * against the oracle run on the BF16-rounded projections (the data the GPU
-  path actually holds), rel-L2 <= 5e-3: what is left is the rounding of the
-  backprojected ray values, each piece's weight times a value with 8
-  significant bits (relative error <= 2^-9), which perturbs A^T by at most
-  2^-9 ~ 2e-3 per term, and the handful of Krylov steps amplifies that at
-  most a few times;
-* the reconstruction's update x - x_p against the oracle's on the
-  BF16-rounded data, rel-L2 <= 5e-3: the update is small beside the volume,
-  so the same per-term rounding shows more in it;
+  path actually holds), the volume and the update x - x_p each within
+  rel-L2 1e-3, the FP32 bound: what is left beside the FP32 arithmetic is
+  the rounding of the re-orthogonalisation basis (8 significant bits,
+  relative error <= 2^-9 per entry), and it enters only through the
+  Gram-Schmidt corrections, which are small because each new v is already
+  nearly orthogonal to the earlier ones;
+* against the oracle on the exact projections, rel-L2 <= 5e-3: the data's
+  own rounding (<= 2^-9 per value) passes through the solve;
 * against the ground truth: the image error of the BF16 path is within 1 % of
   the FP64 oracle's own image error."""
 import numpy as np
@@ -22,8 +22,8 @@ import phantoms as P
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL_BF16 = 5e-3
-TOL_BF16_UPD = 5e-3
+TOL_BF16_DATA = 1e-3  # against the oracle on the BF16-rounded projections
+TOL_BF16 = 5e-3       # against the oracle on the exact projections
 
 
 @pytest.fixture(scope="module")
@@ -68,9 +68,9 @@ def test_bf16_storage_against_oracle_and_truth(pk, c1, solver, record_property):
     record_property("rel_l2_vs_oracle_bf16_data", rel_l2(x, ref16))
     record_property("rel_l2_vs_oracle_exact_data", rel_l2(x, ref))
     record_property("rel_l2_update_vs_oracle_bf16_data", upd)
-    assert rel_l2(x, ref16) <= TOL_BF16, rel_l2(x, ref16)
+    assert rel_l2(x, ref16) <= TOL_BF16_DATA, rel_l2(x, ref16)
+    assert upd <= TOL_BF16_DATA, upd
     assert rel_l2(x, ref) <= TOL_BF16, rel_l2(x, ref)
-    assert upd <= TOL_BF16_UPD, upd
     e64, e16 = rel_l2(ref, truth), rel_l2(x, truth)
     assert e16 <= 1.01 * e64, (e16, e64)
 
