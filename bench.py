@@ -729,9 +729,10 @@ def run_serving(args):
                 "scans_per_s": args.requests / span, "makespan_s": span}
 
     # served: the request loop (FP32 storage, then BF16 storage with BF16 inputs)
-    def served_arm(bf16, order=pk.ORDER_ADAPTIVE):
+    def served_arm(bf16, order=pk.ORDER_ADAPTIVE, max_group=1):
         outs = outbufs()
-        srv = pk.Server(max_batch=8, max_running=2, use_graphs=True, order=order)
+        srv = pk.Server(max_batch=8, max_running=2, use_graphs=True, order=order,
+                        max_group=max_group)
         prm = []
         for k, (p, d) in enumerate(zip(pats, data)):
             srv.add_patient(k, p["geometry"], d["prior"])
@@ -765,7 +766,8 @@ def run_serving(args):
         if any(x["status"] != 0 for x in st):
             raise RuntimeError("served request failed")
         res = summary([x["total_ms"] for x in st], span)
-        res.update(max_batch=8, max_running=2, graphs=True, storage="bf16" if bf16 else "f32",
+        res.update(max_batch=8, max_running=2, max_group=max_group, graphs=True,
+                   storage="bf16" if bf16 else "f32",
                    order={pk.ORDER_FIFO: "fifo", pk.ORDER_RESPONSE_RATIO: "response_ratio"}.get(
                        order, "adaptive"),
                    mean_batch=args.requests / max(sstats["batches"] - warm["batches"], 1),
@@ -774,6 +776,7 @@ def run_serving(args):
 
     served, served16 = served_arm(False), served_arm(True)
     served_rr = served_arm(False, pk.ORDER_RESPONSE_RATIO)
+    served_grp = served_arm(False, max_group=4)
     clk = clocks.stop()
     plain = summary(lat_plain, span_plain)
     line = {
@@ -789,6 +792,7 @@ def run_serving(args):
         "served": served,
         "served_bf16": served16,
         "served_response_ratio": served_rr,
+        "served_grouped": served_grp,
         "plain_one_at_a_time": plain,
         "clocks": clk,
         "input_generation_s": t_in,

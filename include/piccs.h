@@ -242,6 +242,25 @@ int piccs_stage(piccs_ctx *ctx, int slot, const float *proj, int from_host);
  * patterns); the run must then use PICCS_STORAGE_BF16. */
 int piccs_stage_bf16(piccs_ctx *ctx, int slot, const void *proj, int from_host);
 int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph);
+
+/* The staged reconstructions of several contexts -- scans of different
+ * geometries, e.g. of different patients -- run together (Sec. 3's repeated
+ * scans of several patients served at once): the same steps in lockstep, every
+ * product with A and with A^T one kernel launch for all of them (their CTA
+ * index spaces concatenated, each CTA finding its scan in a by-value table of
+ * geometries and buffers), every other kernel per context.  ctxs[i] runs its
+ * first nactive[i] staged slots, all with `params`; 1 <= n <= 8, distinct
+ * contexts on one device.  Each result is bit for bit the one
+ * piccs_run_staged gives that context alone.  The work is enqueued on
+ * ctxs[0]'s stream, after everything already enqueued on the others'
+ * streams (their staging copies); their streams then wait for it (their
+ * unstaging copies).  use_graph: one CUDA graph per (contexts, nactive,
+ * params), kept by ctxs[0] (captured as in piccs_run_staged); a group's
+ * kernels are counted in ctxs[0]'s profile.  Errors: PICCS_EINVAL (bad
+ * arguments, a member's staged data or prior), PICCS_ENOMEM (a member's
+ * basis), PICCS_ECUDA; the message is on ctxs[0]. */
+int piccs_run_staged_group(piccs_ctx *const *ctxs, const int *nactive, int n,
+                           const piccs_params *params, int use_graph);
 int piccs_unstage(piccs_ctx *ctx, int slot, float *vol, int to_host);
 
 /* Forward projection d_proj = A d_vol (Eq. 1): N floats from M floats (each

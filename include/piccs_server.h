@@ -29,9 +29,18 @@
  *     is small (estimated below 25 ms of device time per scan); a scan that
  *     fills the GPU on its own runs alone, since overlapping it would only
  *     stretch both batches;
+ *   - scans of different sizes together: when the session going next has a
+ *     short scan (estimated below 200 ms) at the head of its queue, up to
+ *     max_group - 1 further idle sessions -- other patients, other
+ *     geometries -- whose oldest requests have the same parameters join it,
+ *     in issue order, each with its batch: the group runs as one
+ *     reconstruction in lockstep, every product with A and with A^T one
+ *     kernel launch for all of them (piccs_run_staged_group), and counts as
+ *     one batch in flight;
  *   - captured launches: for scans estimated below 200 ms (where launch
  *     costs matter), a session records the launch sequence of each
- *     (parameters, batch size) pair once as a CUDA graph and replays it.
+ *     (parameters, batch size) pair once as a CUDA graph and replays it;
+ *     a group's sequence is one graph per (sessions, batch sizes, parameters).
  *
  * All calls are thread-safe.  A worker thread owned by the server issues
  * every CUDA call for the sessions on the device that was current when the
@@ -58,6 +67,8 @@ typedef struct {
     int max_running;    /* batches in flight at once (>= 1) */
     int use_graphs;     /* replay captured CUDA graphs for short scans (0: never) */
     int order;          /* PICCS_ORDER_*: which idle session's queue goes next */
+    int max_group;      /* sessions of different patients run as one group
+                           (0 or 1: never; at most 8) -- see above */
 } piccs_server_config;
 
 /* Issue order among idle sessions with queued requests: by the highest
@@ -84,6 +95,7 @@ typedef struct {
     long long sessions_made;   /* sessions created (including re-creations) */
     long long evictions;       /* sessions evicted to admit others */
     size_t hbm_in_use;         /* bytes held by resident sessions */
+    long long group_runs;      /* issues that ran several sessions as one group */
 } piccs_server_stats;
 
 /* Start a server (and its worker thread).  PICCS_EINVAL on a bad config. */

@@ -68,7 +68,7 @@ class piccs_stats(C.Structure):
 
 class piccs_server_config(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("max_running", C.c_int),
-                ("use_graphs", C.c_int), ("order", C.c_int)]
+                ("use_graphs", C.c_int), ("order", C.c_int), ("max_group", C.c_int)]
 
 
 class piccs_request_stats(C.Structure):
@@ -80,7 +80,7 @@ class piccs_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
                 ("batches", C.c_longlong), ("graph_replays", C.c_longlong),
                 ("sessions_made", C.c_longlong), ("evictions", C.c_longlong),
-                ("hbm_in_use", C.c_size_t)]
+                ("hbm_in_use", C.c_size_t), ("group_runs", C.c_longlong)]
 
 
 KERNEL_CLASSES = ("forward", "adjoint", "reg", "vector", "scalar")
@@ -107,6 +107,7 @@ def _load():
         "piccs_stage": (i, [vp, i, vp, i]),
         "piccs_stage_bf16": (i, [vp, i, vp, i]),
         "piccs_run_staged": (i, [vp, i, P, i]),
+        "piccs_run_staged_group": (i, [C.POINTER(vp), C.POINTER(i), i, P, i]),
         "piccs_unstage": (i, [vp, i, vp, i]),
         "piccs_server_create": (i, [C.POINTER(vp), C.POINTER(piccs_server_config)]),
         "piccs_server_destroy": (None, [vp]),
@@ -146,7 +147,8 @@ EXPORTED = ("piccs_create", "piccs_destroy", "piccs_last_error", "piccs_set_stre
             "piccs_reg_weights", "piccs_reg_normal", "piccs_profile_enable",
             "piccs_profile_read", "piccs_reg_normal_noalloc", "piccs_create_batched",
             "piccs_query_workspace_batched", "piccs_report_slot", "piccs_set_prior_broadcast",
-            "piccs_stage", "piccs_stage_bf16", "piccs_run_staged", "piccs_unstage", "piccs_server_create",
+            "piccs_stage", "piccs_stage_bf16", "piccs_run_staged", "piccs_run_staged_group", "piccs_unstage",
+            "piccs_server_create",
             "piccs_server_destroy", "piccs_server_last_error", "piccs_server_add_patient",
             "piccs_server_submit", "piccs_server_wait", "piccs_server_get_stats")
 
@@ -347,6 +349,18 @@ def piccs_reg_normal_noalloc(nx, ny, nz, d_omega, lambda2_piple, d_z, d_out, d_r
                                          _ptr(d_out, n, "out"), rho_ptr, _stream_handle(stream)))
 
 
+def run_staged_group(contexts, nactive, params, graph=True):
+    """Staged reconstructions of several contexts (different geometries) run
+    together: every projector product one launch for all of them
+    (piccs_run_staged_group).  contexts: Context objects; nactive: staged
+    slots per context."""
+    n = len(contexts)
+    hs = (C.c_void_p * n)(*[c.h for c in contexts])
+    na = (C.c_int * n)(*[int(k) for k in nactive])
+    rc = _lib.piccs_run_staged_group(hs, na, n, C.byref(params), 1 if graph else 0)
+    _check(rc, contexts[0].h if n else None)
+
+
 def piccs_profile_enable(ctx, timing=True):
     _check(_lib.piccs_profile_enable(ctx, 1 if timing else 0), ctx)
 
@@ -503,12 +517,15 @@ def _check_srv(rc, srv):
 
 class Server:
     """A request loop for repeated scans: per-patient device sessions admitted
-    by HBM footprint, continuous batching, overlapped batches, CUDA graphs.
-    Buffers handed to submit() are kept referenced until wait() returns."""
+    by HBM footprint, continuous batching, overlapped batches, groups of
+    patients' scans of different sizes run in shared launches (max_group),
+    CUDA graphs.  Buffers handed to submit() are kept referenced until wait()
+    returns."""
 
-    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True, order=2):
+    def __init__(self, hbm_budget=0, max_batch=8, max_running=4, use_graphs=True, order=2,
+                 max_group=1):
         cfg = piccs_server_config(int(hbm_budget), int(max_batch), int(max_running),
-                                  1 if use_graphs else 0, int(order))
+                                  1 if use_graphs else 0, int(order), int(max_group))
         h = C.c_void_p()
         _check_srv(_lib.piccs_server_create(C.byref(h), C.byref(cfg)), None)
         self.h = h.value

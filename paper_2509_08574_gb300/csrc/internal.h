@@ -114,6 +114,49 @@ struct LsqrScalars {
 
 enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_LSQR = 2, FWD_RESID16 = 3 };
 
+// Scans of different geometries projected in one launch ("groups"): each job
+// is one context's part -- its geometry, ray tables and buffers (slot 0's;
+// the context's slots sstride bytes apart), nslot slots of nb blocks each.
+// The table goes to the kernel by value (kernel parameters), so a captured
+// CUDA graph keeps its own copy.
+constexpr int kMaxGroup = 8;
+struct FwdJob {
+    ProjGeom g;
+    const ColParams *cols;
+    const float2 *vr;
+    const int4 *cells;
+    const float *vol;
+    float *out;
+    const float *aux;
+    double *partials;
+    int *nonfinite;
+    float *ra, *aw;
+    long long sstride;
+    int nslot, nb;
+};
+struct FwdGroup {
+    FwdJob job[kMaxGroup];
+    int b0[kMaxGroup];  // the job's first block in the grid
+    int n;
+};
+struct AdjJob {
+    ProjGeom g;
+    const ColParams *cols;
+    const float2 *vr;
+    const int *hit_ptr;
+    const CellHit *hits;
+    const float *proj;
+    float *rs;
+    float *vol;
+    long long sstride;
+    int nslot, nb;
+};
+struct AdjGroup {
+    AdjJob job[kMaxGroup];
+    int b0[kMaxGroup];
+    int n;
+};
+
 // ---- projector (kernels_project.cu) ----
 int project_blocks(const ProjGeom &g);
 // vr[iv] = {v, 1/v} per detector row (1e30 for v = 0)
@@ -133,6 +176,12 @@ inline long long adjoint_rs_floats(long long N, long long ncol) { return N + 2 *
 cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float2 *vr,
                            const int *hit_ptr, const CellHit *hits, const float *proj, float *rs,
                            float *vol, cudaStream_t st, Slots sl = Slots{1, 0});
+// The same for 1 <= n <= kMaxGroup jobs in one launch per kernel (the ray
+// scaling stays one launch per job): each job's result is bit for bit the
+// one launch_forward / launch_forward_lsqr / launch_adjoint gives it.  Every
+// job's mode is `mode`; partials (per job) may be null only for all jobs.
+cudaError_t launch_forward_group(const FwdJob *jobs, int n, int mode, cudaStream_t st);
+cudaError_t launch_adjoint_group(const AdjJob *jobs, int n, cudaStream_t st);
 // n FP32 values per slot -> BF16 (round to nearest even)
 cudaError_t launch_to_bf16(long long n, const float *src, long long src_stride, void *dst,
                            long long dst_stride, int nslot, cudaStream_t st);

@@ -89,12 +89,11 @@ __device__ __forceinline__ float rcp_approx(float x)
 // row p (its mirror; absent when both are the middle row of an odd nv).
 __device__ __forceinline__ int npairs_rows(int nv) { return (nv + 1) >> 1; }
 
-// CTA = one detector column (j, iu) and kRowGroups x 32 row pairs
-__device__ __forceinline__ void decode_block(const ProjGeom &G, int &col, int &p)
+// CTA b = one detector column (j, iu) and kRowGroups x 32 row pairs
+__device__ __forceinline__ void decode_block(const ProjGeom &G, int b, int &col, int &p)
 {
     const int np = npairs_rows(G.nv);
     const int nrgb = (np + 32 * kRowGroups - 1) / (32 * kRowGroups);
-    const int b = blockIdx.x;
     col = b / nrgb;
     p = ((b - col * nrgb) * kRowGroups + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
 }
@@ -167,24 +166,17 @@ __device__ __forceinline__ void walk_pair(const ProjGeom &G, const ColParams &cp
 
 // 8 CTAs of 256 threads per SM (32 registers): the walk's gathers need the
 // full occupancy to hide their latency once the volume no longer fits in L2
+// One CTA (block blk of one scan) of the forward; the buffers are the scan's.
 template <int MODE, bool NORM, bool MULTI>
-__global__ void __launch_bounds__(256, 8)
-fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-           const int4 *__restrict__ cells, const float *__restrict__ vol,
-           float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
-           int *__restrict__ nonfinite, float *__restrict__ ra, float *__restrict__ aw,
-           long long sstride)
+__device__ __forceinline__ void fwd_block(const ProjGeom &G, const ColParams *__restrict__ cols,
+                                          const float2 *__restrict__ vr,
+                                          const int4 *__restrict__ cells,
+                                          const float *__restrict__ vol, float *__restrict__ out,
+                                          const float *__restrict__ aux,
+                                          double *__restrict__ partials,
+                                          int *__restrict__ nonfinite, float *__restrict__ ra,
+                                          float *__restrict__ aw, int blk)
 {
-    if (sstride) {  // slot blockIdx.y of a batch
-        const long long so = blockIdx.y * sstride;
-        vol = slot_ptr(vol, so);
-        out = slot_ptr(out, so);
-        aux = slot_ptr(aux, so);
-        partials = slot_ptr(partials, so);
-        nonfinite = slot_ptr(nonfinite, so);
-        ra = slot_ptr(ra, so);
-        aw = slot_ptr(aw, so);
-    }
     if (MODE == FWD_LSQR && aux[2] != 0.f) return;  // the Krylov cycle has stopped
     __shared__ double red[kRowGroups];  // NORM: the warps' partial sums
     __shared__ unsigned warps_done;
@@ -193,7 +185,7 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
         __syncthreads();  // before any warp can finish
     }
     int col, p;
-    decode_block(G, col, p);
+    decode_block(G, blk, col, p);
     const bool pair_ok = p < npairs_rows(G.nv);
     const int iva = G.nv - 1 - p;               // upper row (v >= 0)
     const bool has_b = pair_ok && p != iva;     // lower mirror row p
@@ -271,10 +263,51 @@ fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restr
                 double t = 0.0;
 #pragma unroll
                 for (int w = 0; w < kRowGroups; ++w) t += rv[w];
-                partials[blockIdx.x] = t;
+                partials[blk] = t;
             }
         }
     }
+}
+
+// One scan, or the scans of a batch (slot blockIdx.y, buffers sstride bytes apart)
+template <int MODE, bool NORM, bool MULTI>
+__global__ void __launch_bounds__(256, 8)
+fwd_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
+           const int4 *__restrict__ cells, const float *__restrict__ vol,
+           float *__restrict__ out, const float *__restrict__ aux, double *__restrict__ partials,
+           int *__restrict__ nonfinite, float *__restrict__ ra, float *__restrict__ aw,
+           long long sstride)
+{
+    const long long so = blockIdx.y * sstride;
+    fwd_block<MODE, NORM, MULTI>(G, cols, vr, cells, slot_ptr(vol, so), slot_ptr(out, so),
+                                 slot_ptr(aux, so), slot_ptr(partials, so),
+                                 slot_ptr(nonfinite, so), slot_ptr(ra, so), slot_ptr(aw, so),
+                                 blockIdx.x);
+}
+
+// Scans of different geometries in one grid: the jobs' blocks one after
+// another (job m: slots x blocks per slot from block b0); each CTA finds its
+// job and runs the same block as the single-scan kernel, so every scan's
+// result is bit for bit its standalone result.
+__device__ __forceinline__ int find_job(int b, const int *b0, int n)
+{
+    int m = 0;
+    while (m + 1 < n && b >= b0[m + 1]) ++m;
+    return m;
+}
+
+template <int MODE, bool NORM, bool MULTI>
+__global__ void __launch_bounds__(256, 8) fwd_group_kernel(const FwdGroup grp)
+{
+    const int m = find_job(blockIdx.x, grp.b0, grp.n);
+    const FwdJob &J = grp.job[m];
+    const int local = blockIdx.x - grp.b0[m];
+    const int slot = local / J.nb;
+    const long long so = slot * J.sstride;
+    fwd_block<MODE, NORM, MULTI>(J.g, J.cols, J.vr, J.cells, slot_ptr(J.vol, so),
+                                 slot_ptr(J.out, so), slot_ptr(J.aux, so), slot_ptr(J.partials, so),
+                                 slot_ptr(J.nonfinite, so), slot_ptr(J.ra, so), slot_ptr(J.aw, so),
+                                 local - slot * J.nb);
 }
 
 // rs = proj * sec, per ray (the adjoint's gather then needs no square root).
@@ -290,7 +323,7 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
     proj = slot_ptr(proj, blockIdx.y * sstride);
     rs = slot_ptr(rs, blockIdx.y * sstride);
     int col, p;
-    decode_block(G, col, p);
+    decode_block(G, blockIdx.x, col, p);
     if (p >= npairs_rows(G.nv)) return;
     const int j = col / G.nu, iu = col - j * G.nu;
     const long long base = (long long)j * G.sj + (long long)iu * G.su;
@@ -318,17 +351,17 @@ scale_rays_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
 // EVEN (even nv and nz): no row has v = 0 and no layer straddles z = 0, so
 // every upper layer is crossed by the upper rows only (iv >= nv / 2), upwards;
 // the ray values are read as mirror-row pairs (scale_rays_kernel<true>).
+// One CTA: xy voxel column `cell`, layer-pair chunk `chunk`, of one scan.
 template <bool EVEN>
-__global__ void __launch_bounds__(kGatherThreads, PICCS_GATHER_MIN_CTAS)
-adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-                  const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
-                  const float *__restrict__ rs, float *__restrict__ vol, long long sstride)
+__device__ __forceinline__ void adj_gather_block(const ProjGeom &G, const ColParams *__restrict__ cols,
+                                                 const float2 *__restrict__ vr,
+                                                 const int *__restrict__ hit_ptr,
+                                                 const CellHit *__restrict__ hits,
+                                                 const float *__restrict__ rs,
+                                                 float *__restrict__ vol, int cell, int chunk)
 {
-    rs = slot_ptr(rs, blockIdx.z * sstride);
-    vol = slot_ptr(vol, blockIdx.z * sstride);
     constexpr int L = kLayersPerThread;
-    const int cell = blockIdx.x;
-    const int pb = blockIdx.y * kGatherThreads * L + threadIdx.x;
+    const int pb = chunk * kGatherThreads * L + threadIdx.x;
     const int nlp = (G.nz + 1) >> 1;  // layer pairs (the middle layer of an odd nz pairs with itself)
     float zlo[L], accu[L], accd[L];
     bool pok[L];
@@ -427,6 +460,35 @@ adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
         colv[ku] += accu[q];
         if (p != ku) colv[p] += accd[q];
     }
+}
+
+// grid: voxel columns x layer-pair chunks x slots
+template <bool EVEN>
+__global__ void __launch_bounds__(kGatherThreads, PICCS_GATHER_MIN_CTAS)
+adj_gather_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
+                  const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
+                  const float *__restrict__ rs, float *__restrict__ vol, long long sstride)
+{
+    const long long so = blockIdx.z * sstride;
+    adj_gather_block<EVEN>(G, cols, vr, hit_ptr, hits, slot_ptr(rs, so), slot_ptr(vol, so),
+                           blockIdx.x, blockIdx.y);
+}
+
+// scans of different geometries in one grid (see fwd_group_kernel); job m's
+// blocks are slots x chunks x voxel columns, voxel columns fastest
+template <bool EVEN>
+__global__ void __launch_bounds__(kGatherThreads, PICCS_GATHER_MIN_CTAS)
+adj_gather_group_kernel(const AdjGroup grp)
+{
+    const int m = find_job(blockIdx.x, grp.b0, grp.n);
+    const AdjJob &J = grp.job[m];
+    const int local = blockIdx.x - grp.b0[m];
+    const int ncell = J.g.nx * J.g.ny, per_slot = J.nb;
+    const int slot = local / per_slot, rem = local - slot * per_slot;
+    const int chunk = rem / ncell;
+    const long long so = slot * J.sstride;
+    adj_gather_block<EVEN>(J.g, J.cols, J.vr, J.hit_ptr, J.hits, slot_ptr(J.rs, so),
+                           slot_ptr(J.vol, so), rem - chunk * ncell, chunk);
 }
 
 // ---------------------------------------------------------------------------
@@ -591,15 +653,15 @@ __device__ __forceinline__ void prefix_planes(std::integer_sequence<int, PL...>,
 // hz = nz/2, i.e. the planes kc = l R .. l R + R.  The crossings of the
 // column are prepared 32 at a time, one per lane, in shared memory.
 template <int R>
-__global__ void __launch_bounds__(32 * kPrefixWarps)
-adj_prefix_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
-                  const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
-                  const float2 *__restrict__ pq, float *__restrict__ vol, long long sstride)
+__device__ __forceinline__ void adj_prefix_block(const ProjGeom &G, const ColParams *__restrict__ cols,
+                                                 const float2 *__restrict__ vr,
+                                                 const int *__restrict__ hit_ptr,
+                                                 const CellHit *__restrict__ hits,
+                                                 const float2 *__restrict__ pq,
+                                                 float *__restrict__ vol, int blk)
 {
-    pq = slot_ptr(pq, blockIdx.y * sstride);
-    vol = slot_ptr(vol, blockIdx.y * sstride);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cell = blockIdx.x * kPrefixWarps + w;
+    const int cell = blk * kPrefixWarps + w;
     if (cell >= G.nx * G.ny) return;  // whole warps; only __syncwarp below
     const int h = G.nv >> 1, hz = G.nz >> 1, nv = G.nv;
     const float fnv = (float)nv;
@@ -646,6 +708,32 @@ adj_prefix_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *
             colv[G.nz - 1 - ku] += ad[q];
         }
     }
+}
+
+// grid: blocks of kPrefixWarps voxel columns x slots
+template <int R>
+__global__ void __launch_bounds__(32 * kPrefixWarps)
+adj_prefix_kernel(ProjGeom G, const ColParams *__restrict__ cols, const float2 *__restrict__ vr,
+                  const int *__restrict__ hit_ptr, const CellHit *__restrict__ hits,
+                  const float2 *__restrict__ pq, float *__restrict__ vol, long long sstride)
+{
+    const long long so = blockIdx.y * sstride;
+    adj_prefix_block<R>(G, cols, vr, hit_ptr, hits, slot_ptr(pq, so), slot_ptr(vol, so),
+                        blockIdx.x);
+}
+
+// scans of different geometries (and the same R) in one grid
+template <int R>
+__global__ void __launch_bounds__(32 * kPrefixWarps) adj_prefix_group_kernel(const AdjGroup grp)
+{
+    const int m = find_job(blockIdx.x, grp.b0, grp.n);
+    const AdjJob &J = grp.job[m];
+    const int local = blockIdx.x - grp.b0[m];
+    const int slot = local / J.nb;
+    const long long so = slot * J.sstride;
+    adj_prefix_block<R>(J.g, J.cols, J.vr, J.hit_ptr, J.hits,
+                        reinterpret_cast<const float2 *>(slot_ptr(J.rs, so)), slot_ptr(J.vol, so),
+                        local - slot * J.nb);
 }
 
 }  // namespace
@@ -759,6 +847,117 @@ cudaError_t launch_adjoint(const ProjGeom &g, const ColParams *cols, const float
         scale_rays_kernel<false><<<sgrid, 256, 0, st>>>(g, cols, vr, proj, rs, sl.stride);
         adj_gather_kernel<false><<<grid, kGatherThreads, 0, st>>>(g, cols, vr, hit_ptr, hits, rs,
                                                                   vol, sl.stride);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_group(const FwdJob *jobs, int n, int mode, cudaStream_t st)
+{
+    if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+    FwdGroup grp{};
+    long long total = 0;
+    bool multi = false;
+    const bool norm = jobs[0].partials != nullptr;
+    for (int i = 0; i < n; ++i) {
+        grp.job[i] = jobs[i];
+        grp.job[i].nb = project_blocks(jobs[i].g);
+        grp.b0[i] = (int)total;
+        total += (long long)grp.job[i].nb * jobs[i].nslot;
+        multi |= jobs[i].g.multi != 0;
+        if ((jobs[i].partials != nullptr) != norm) return cudaErrorInvalidValue;
+    }
+    grp.n = n;
+    if (total <= 0) return cudaSuccess;
+    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned nb = (unsigned)total;
+#define PICCS_FWDG(M, NORM)                                                         \
+    do {                                                                            \
+        if (multi) fwd_group_kernel<M, NORM, true><<<nb, 256, 0, st>>>(grp);        \
+        else fwd_group_kernel<M, NORM, false><<<nb, 256, 0, st>>>(grp);             \
+    } while (0)
+    switch (mode) {
+    case FWD_RESID:
+        if (norm) PICCS_FWDG(FWD_RESID, true); else PICCS_FWDG(FWD_RESID, false);
+        break;
+    case FWD_RESID16:
+        if (norm) PICCS_FWDG(FWD_RESID16, true); else PICCS_FWDG(FWD_RESID16, false);
+        break;
+    case FWD_LSQR:
+        if (!norm) return cudaErrorInvalidValue;
+        PICCS_FWDG(FWD_LSQR, true);
+        break;
+    default:
+        if (norm) PICCS_FWDG(FWD_PLAIN, true); else PICCS_FWDG(FWD_PLAIN, false);
+    }
+#undef PICCS_FWDG
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_group(const AdjJob *jobs, int n, cudaStream_t st)
+{
+    if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+    // the ray scaling (or prefix sums) of each job, then one gather launch per
+    // gather kind present: candidate (even sizes / general) or prefix sums (R)
+    int kind[kMaxGroup];
+    for (int i = 0; i < n; ++i) {
+        const ProjGeom &g = jobs[i].g;
+        const long long ncol = (long long)g.n_views * g.nu;
+        if (project_blocks(g) <= 0) {
+            kind[i] = -1;
+            continue;
+        }
+        if (adjoint_uses_prefix(g)) {
+            const dim3 pgrid((unsigned)((ncol * 32 + 255) / 256), (unsigned)jobs[i].nslot);
+            ray_prefix_kernel<<<pgrid, 256, 0, st>>>(g, jobs[i].cols, jobs[i].vr, jobs[i].proj,
+                                                     reinterpret_cast<float2 *>(jobs[i].rs),
+                                                     jobs[i].sstride);
+            kind[i] = 10 + ((g.nz >> 1) + 31) / 32;  // prefix, R layers per lane
+        } else {
+            const bool even = (g.nv & 1) == 0 && (g.nz & 1) == 0;
+            const dim3 sgrid((unsigned)project_blocks(g), (unsigned)jobs[i].nslot);
+            if (even)
+                scale_rays_kernel<true><<<sgrid, 256, 0, st>>>(g, jobs[i].cols, jobs[i].vr,
+                                                               jobs[i].proj, jobs[i].rs, jobs[i].sstride);
+            else
+                scale_rays_kernel<false><<<sgrid, 256, 0, st>>>(g, jobs[i].cols, jobs[i].vr,
+                                                                jobs[i].proj, jobs[i].rs, jobs[i].sstride);
+            kind[i] = even ? 1 : 0;
+        }
+    }
+    bool done[kMaxGroup] = {};
+    for (int i = 0; i < n; ++i) {
+        if (done[i] || kind[i] < 0) continue;
+        AdjGroup grp{};
+        long long total = 0;
+        for (int k = i; k < n; ++k) {
+            if (done[k] || kind[k] != kind[i]) continue;
+            done[k] = true;
+            AdjJob J = jobs[k];
+            const int ncell = J.g.nx * J.g.ny;
+            if (kind[i] >= 10) {
+                J.nb = (ncell + kPrefixWarps - 1) / kPrefixWarps;
+            } else {
+                const int per_cta = kGatherThreads * kLayersPerThread;
+                J.nb = ncell * (((J.g.nz + 1) / 2 + per_cta - 1) / per_cta);
+            }
+            grp.job[grp.n] = J;
+            grp.b0[grp.n] = (int)total;
+            total += (long long)J.nb * J.nslot;
+            grp.n += 1;
+        }
+        if (total <= 0) continue;
+        if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+        const unsigned nb = (unsigned)total;
+        switch (kind[i]) {
+        case 0: adj_gather_group_kernel<false><<<nb, kGatherThreads, 0, st>>>(grp); break;
+        case 1: adj_gather_group_kernel<true><<<nb, kGatherThreads, 0, st>>>(grp); break;
+#define PICCS_ADJG(RR) \
+        case 10 + RR: adj_prefix_group_kernel<RR><<<nb, 32 * kPrefixWarps, 0, st>>>(grp); break;
+        PICCS_ADJG(1) PICCS_ADJG(2) PICCS_ADJG(3) PICCS_ADJG(4)
+        PICCS_ADJG(5) PICCS_ADJG(6) PICCS_ADJG(7) PICCS_ADJG(8)
+#undef PICCS_ADJG
+        default: return cudaErrorInvalidValue;
+        }
     }
     return cudaGetLastError();
 }

@@ -7,6 +7,7 @@
 // the device, so a whole reconstruction is enqueued without a round trip.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -69,6 +70,8 @@ struct piccs_ctx {
     std::map<std::string, GraphEntry> graphs;
     long long graph_launches = 0;
     cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot capture)
+    long long uid = 0;        // unique per context of the process (keys of group graphs)
+    long long basis_gen = 0;  // incremented whenever the basis is reallocated
     // kernel accounting
     bool timing = false;
     long long launches[PICCS_KERNEL_CLASSES] = {};
@@ -342,6 +345,8 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
 
     piccs_ctx *ctx = new (std::nothrow) piccs_ctx();
     if (!ctx) return set_err(nullptr, PICCS_ENOMEM, "host allocation failed");
+    static std::atomic<long long> next_uid{1};
+    ctx->uid = next_uid.fetch_add(1);
     ctx->geo = *geometry;
     ctx->angles.assign(geometry->angles_rad, geometry->angles_rad + geometry->n_views);
     ctx->geo.angles_rad = ctx->angles.data();
@@ -629,161 +634,305 @@ static int ensure_basis(piccs_ctx *ctx, int n_inner, int storage)
     ctx->part_dots = static_cast<double *>(mem);
     ctx->basis = static_cast<char *>(mem) + basis_dots_bytes();
     ctx->basis_stride = per_slot;
+    ctx->basis_gen += 1;
     return PICCS_OK;
 }
+
+extern "C++" {  // the enqueue helpers are templates
+
+// The contexts one enqueue advances in lockstep, every kernel on its
+// context's stream (for a group: the same stream for all).  One context, or
+// up to kMaxGroup contexts of different geometries whose projector products
+// share one launch per kernel while every other kernel runs per context.
+struct Run {
+    piccs_ctx *m[kMaxGroup];
+    int n;
+};
+
+#define EACH(R) for (int i_ = 0; i_ < (R).n; ++i_) if (piccs_ctx *ctx = (R).m[i_])
+
+static FwdJob fwd_job(piccs_ctx *c, const float *vol, float *out, const float *aux, double *partials,
+                      int *nonfinite, float *ra = nullptr, float *aw = nullptr)
+{
+    FwdJob j{};
+    j.g = c->pg;
+    j.cols = c->cols;
+    j.vr = c->vr;
+    j.cells = c->cells;
+    j.vol = vol;
+    j.out = out;
+    j.aux = aux;
+    j.partials = partials;
+    j.nonfinite = nonfinite;
+    j.ra = ra;
+    j.aw = aw;
+    j.sstride = (long long)c->slot_bytes;
+    j.nslot = c->nactive;
+    return j;
+}
+
+static AdjJob adj_job(piccs_ctx *c, const float *proj, float *vol)
+{
+    AdjJob j{};
+    j.g = c->pg;
+    j.cols = c->cols;
+    j.vr = c->vr;
+    j.hit_ptr = c->hit_ptr;
+    j.hits = c->hits;
+    j.proj = proj;
+    j.rs = c->rs;
+    j.vol = vol;
+    j.sstride = (long long)c->slot_bytes;
+    j.nslot = c->nactive;
+    return j;
+}
+
+// A = the forward in `mode` of every member (job(ctx) gives its buffers).
+template <class F>
+static int run_forward(const Run &R, int mode, F job)
+{
+    piccs_ctx *lead = R.m[0];
+    if (R.n == 1) {
+        const FwdJob j = job(lead);
+        if (mode == FWD_LSQR)
+            LAUNCH(lead, PICCS_KERNEL_FORWARD,
+                   launch_forward_lsqr(j.g, j.cols, j.vr, j.cells, j.vol, j.out, j.aux, j.ra, j.aw,
+                                       j.partials, lead->stream, SL(lead)));
+        else
+            LAUNCH(lead, PICCS_KERNEL_FORWARD,
+                   launch_forward(j.g, j.cols, j.vr, j.cells, j.vol, j.out, mode, j.aux, j.partials,
+                                  j.nonfinite, lead->stream, SL(lead)));
+        return PICCS_OK;
+    }
+    FwdJob jobs[kMaxGroup];
+    for (int i = 0; i < R.n; ++i) jobs[i] = job(R.m[i]);
+    LAUNCH(lead, PICCS_KERNEL_FORWARD, launch_forward_group(jobs, R.n, mode, lead->stream));
+    return PICCS_OK;
+}
+
+// s = A^T r of every member (the data residual r into the image vector s)
+static int run_adjoint(const Run &R)
+{
+    piccs_ctx *lead = R.m[0];
+    if (R.n == 1) {
+        LAUNCH(lead, PICCS_KERNEL_ADJOINT, launch_adjoint(lead->pg, lead->cols, lead->vr, lead->hit_ptr,
+                                                          lead->hits, lead->r, lead->rs, lead->s,
+                                                          lead->stream, SL(lead)));
+        return PICCS_OK;
+    }
+    AdjJob jobs[kMaxGroup];
+    for (int i = 0; i < R.n; ++i) jobs[i] = adj_job(R.m[i], R.m[i]->r, R.m[i]->s);
+    LAUNCH(lead, PICCS_KERNEL_ADJOINT, launch_adjoint_group(jobs, R.n, lead->stream));
+    return PICCS_OK;
+}
+
+#define RUN_TRY(call)                 \
+    do {                              \
+        int rc_ = (call);             \
+        if (rc_ != PICCS_OK) return rc_; \
+    } while (0)
 
 // One IRN cycle with LSQR as the inner solver (weights already frozen in
 // omega, c).  Buffers: uA in r, the data residual b - A x in q (kept current
 // through A w in aw, so only the first cycle projects x), vhat in p, w in g,
 // z alternating between t and w2sq (free once c is formed), s = the
-// regularisation part of A~^T u plus, after the adjoint, A^T uA.
-static int enqueue_lsqr_cycle(piccs_ctx *ctx, const float *d_b, const piccs_params *p, int cycle)
+// regularisation part of A~^T u plus, after the adjoint, A^T uA.  d_b(ctx):
+// the member's projections.
+template <class B>
+static int enqueue_lsqr_cycle(const Run &R, B d_b, const piccs_params *p, int cycle)
 {
-    cudaStream_t st = ctx->stream;
-    const long long M = ctx->M;
     const float l2p = lam2_piple(p);
     const bool reorth = p->solver == PICCS_SOLVER_LSQR_REORTH;
     const bool bf16 = p->storage == PICCS_STORAGE_BF16;
     const bool prior_rhs = p->variant == PICCS_VARIANT_PICCS || p->variant == PICCS_VARIANT_PIPLE;
-    LsqrScalars *ls = ctx->ls;
-    float *z[2] = {ctx->t, ctx->w2sq};
     int cur = 0;
+    auto zbuf = [](piccs_ctx *c, int k) { return k == 0 ? c->t : c->w2sq; };
     // beta_1 u_1 = b~ - A~ x: uA = b - A x, z = -x, sigma = 1
     if (cycle == 0)
-        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->q,
-                                                         bf16 ? FWD_RESID16 : FWD_RESID, d_b, nullptr,
-                                                         &ctx->ks->nonfinite, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ls,
-                                                       ctx->part_vec, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ls, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 1, ctx->x, nullptr, z[cur], nullptr, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, z[cur], ctx->omega, l2p, ctx->c,
-                                                   prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
-                                                   ctx->part_vol, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec,
-                                                               ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
+        RUN_TRY(run_forward(R, bf16 ? FWD_RESID16 : FWD_RESID, [&](piccs_ctx *c) {
+            return fwd_job(c, c->x, c->q, d_b(c), nullptr, &c->ks->nonfinite);
+        }));
+    EACH(R) {
+        cudaStream_t st = ctx->stream;
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_rinit(ctx->N, cycle > 0, ctx->q, ctx->aw, ctx->r, ctx->ls,
+                                                           ctx->part_vec, st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_reset(ctx->ks, ctx->ls, st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 1, ctx->x, nullptr, zbuf(ctx, cur), nullptr,
+                                                           st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 1, zbuf(ctx, cur), ctx->omega, l2p, ctx->c,
+                                                       prior_rhs ? ctx->xprior : nullptr, ctx->s, nullptr,
+                                                       ctx->part_vol, st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ctx->ls, 1, ctx->part_vec,
+                                                                   ctx->n_part_vec, ctx->part_vol,
+                                                                   ctx->n_part_vol, st, SL(ctx)));
+    }
     // alpha_1 v_1 = A~^T u_1
-    LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r,
-                                                     ctx->rs, ctx->s, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr, ls,
-                                                    ctx->part_vec, st, SL(ctx)));
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 1, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
+    RUN_TRY(run_adjoint(R));
+    EACH(R) {
+        cudaStream_t st = ctx->stream;
+        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(ctx->M, 1, 0, ctx->x, ctx->g, ctx->p, ctx->s, nullptr,
+                                                        ctx->ls, ctx->part_vec, st, SL(ctx)));
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ctx->ls, 1, ctx->part_vec,
+                                                                    ctx->n_part_vec, st, SL(ctx)));
+    }
     for (int i = 1; i <= p->n_inner; ++i) {
         const bool last = i == p->n_inner;
         // beta_{i+1} u_{i+1} = A~ v_i - alpha_i u_i
-        LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward_lsqr(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p,
-                                                              ctx->r, ls->fwd, ctx->q, ctx->aw, ctx->part_fwd, st, SL(ctx)));
-        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 0, ctx->p, z[cur], z[cur ^ 1], ls->ureg, st,
+        RUN_TRY(run_forward(R, FWD_LSQR, [&](piccs_ctx *c) {
+            return fwd_job(c, c->p, c->r, c->ls->fwd, c->part_fwd, nullptr, c->q, c->aw);
+        }));
+        EACH(R) {
+            cudaStream_t st = ctx->stream;
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_zstep(ctx->vd, 0, ctx->p, zbuf(ctx, cur),
+                                                               zbuf(ctx, cur ^ 1), ctx->ls->ureg, st, SL(ctx)));
+            LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, zbuf(ctx, cur ^ 1), ctx->omega, l2p, ctx->c,
+                                                           nullptr, ctx->s, ctx->ls->ureg, ctx->part_vol, st,
                                                            SL(ctx)));
-        cur ^= 1;
-        LAUNCH(ctx, PICCS_KERNEL_REG, launch_lsqr_ureg(ctx->vd, 0, z[cur], ctx->omega, l2p, ctx->c, nullptr,
-                                                       ctx->s, ls->ureg, ctx->part_vol, st, SL(ctx)));
-        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ls, 0, ctx->part_fwd, ctx->n_part_fwd,
-                                                                   ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
-        // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
-        if (!last)
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits,
-                                                             ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
-        const long long ldb = lsqr_basis_stride(M);
-        void *bv = (reorth && !last)
-                       ? static_cast<char *>(ctx->basis) + (size_t)(i - 1) * ldb * (bf16 ? 2 : sizeof(float))
-                       : nullptr;
-        const long long bst = (long long)ctx->basis_stride;
-        LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 0, last, ctx->x, ctx->g, ctx->p, ctx->s, bv, ls,
-                                                        ctx->part_vec, st, SL(ctx), bst, bf16));
-        if (last) break;
-        if (reorth) {
-            for (int pass = 0; pass < 2; ++pass) {
-                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ls, ctx->part_dots, st,
-                                                                  SL(ctx), bst, bf16));
-                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ls, ctx->part_dots, st, SL(ctx), bst));
-                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_sub(M, ldb, i, ctx->basis, ctx->p, ls,
-                                                                 pass == 1 ? ctx->part_vec : nullptr, st, SL(ctx),
-                                                                 bst, bf16));
-            }
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_beta(ctx->ks, ctx->ls, 0, ctx->part_fwd,
+                                                                       ctx->n_part_fwd, ctx->part_vol,
+                                                                       ctx->n_part_vol, st, SL(ctx)));
         }
-        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ls, 0, ctx->part_vec, ctx->n_part_vec, st, SL(ctx)));
+        cur ^= 1;
+        // alpha_{i+1} v_{i+1} = A~^T u_{i+1} - beta_{i+1} v_i (not needed after the last step)
+        if (!last) RUN_TRY(run_adjoint(R));
+        EACH(R) {
+            cudaStream_t st = ctx->stream;
+            const long long M = ctx->M;
+            const long long ldb = lsqr_basis_stride(M);
+            void *bv = (reorth && !last)
+                           ? static_cast<char *>(ctx->basis) + (size_t)(i - 1) * ldb * (bf16 ? 2 : sizeof(float))
+                           : nullptr;
+            const long long bst = (long long)ctx->basis_stride;
+            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_vx(M, 0, last, ctx->x, ctx->g, ctx->p, ctx->s, bv,
+                                                            ctx->ls, ctx->part_vec, st, SL(ctx), bst, bf16));
+            if (last) continue;
+            if (reorth) {
+                for (int pass = 0; pass < 2; ++pass) {
+                    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_dots(M, ldb, i, ctx->basis, ctx->p, ctx->ls,
+                                                                      ctx->part_dots, st, SL(ctx), bst, bf16));
+                    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_fin_dots(i, ctx->ls, ctx->part_dots, st,
+                                                                          SL(ctx), bst));
+                    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_lsqr_sub(M, ldb, i, ctx->basis, ctx->p, ctx->ls,
+                                                                     pass == 1 ? ctx->part_vec : nullptr, st,
+                                                                     SL(ctx), bst, bf16));
+                }
+            }
+            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_lsqr_finalize_alpha(ctx->ks, ctx->ls, 0, ctx->part_vec,
+                                                                        ctx->n_part_vec, st, SL(ctx)));
+        }
+        if (last) break;
     }
     return PICCS_OK;
 }
 
-// d_b: the slots' projections, slot_bytes apart (any pointer for one slot),
-// FP32, or BF16 when p->storage is BF16; d_x0: the slots' initial volumes,
-// x0_pitch bytes apart.
-static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
-                               const float *d_x0, size_t x0_pitch)
+// One IRN-PICCS reconstruction of every member from its device-resident data
+// d_b(ctx) into its x; d_x0: the slots' initial volumes, x0_pitch bytes apart
+// (one context only).  A context's projections are FP32, or BF16 when
+// p->storage is BF16.
+template <class B>
+static int enqueue_reconstruct(const Run &R, B d_b, const piccs_params *p, const float *d_x0,
+                               size_t x0_pitch)
 {
-    cudaStream_t st = ctx->stream;
     const bool bf16 = p->storage == PICCS_STORAGE_BF16;
-    const long long M = ctx->M, N = ctx->N;
     const float l2p = lam2_piple(p);
-    const size_t vb = M * sizeof(float), S = ctx->slot_bytes;
-
-    LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st, SL(ctx)));
-    if (p->x0_mode == PICCS_X0_PRIOR) {
-        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, ctx->xprior, S, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
-    } else if (p->x0_mode == PICCS_X0_ZERO) {
-        CUDA_TRY(ctx, cudaMemset2DAsync(ctx->x, S, 0, vb, ctx->nactive, st));
-    } else {
-        CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, d_x0, x0_pitch, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
+    EACH(R) {
+        cudaStream_t st = ctx->stream;
+        const size_t vb = ctx->M * sizeof(float), S = ctx->slot_bytes;
+        LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_reset_scalars(ctx->ks, st, SL(ctx)));
+        if (p->x0_mode == PICCS_X0_PRIOR) {
+            CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, ctx->xprior, S, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
+        } else if (p->x0_mode == PICCS_X0_ZERO) {
+            CUDA_TRY(ctx, cudaMemset2DAsync(ctx->x, S, 0, vb, ctx->nactive, st));
+        } else {
+            CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->x, S, d_x0, x0_pitch, vb, ctx->nactive, cudaMemcpyDeviceToDevice, st));
+        }
     }
     if (p->solver != PICCS_SOLVER_CGLS) {
-        if (p->solver == PICCS_SOLVER_LSQR_REORTH) {
-            int rc = ensure_basis(ctx, p->n_inner, p->storage);
-            if (rc != PICCS_OK) return rc;
-        }
         if (p->n_inner == 0) {  // no inner step: x stays x0; still flag NaN/Inf in b
-            if (bf16)
-                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite16(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
-            else
-                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(N, d_b, &ctx->ks->nonfinite, st, SL(ctx)));
+            EACH(R) {
+                if (bf16)
+                    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite16(ctx->N, d_b(ctx), &ctx->ks->nonfinite,
+                                                                              ctx->stream, SL(ctx)));
+                else
+                    LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_count_nonfinite(ctx->N, d_b(ctx), &ctx->ks->nonfinite,
+                                                                            ctx->stream, SL(ctx)));
+            }
             return PICCS_OK;
         }
         for (int k = 0; k < p->n_outer; ++k) {
-            int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx));
-            if (rc == PICCS_OK) rc = enqueue_lsqr_cycle(ctx, d_b, p, k);
-            if (rc != PICCS_OK) return rc;
+            EACH(R) RUN_TRY(enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx)));
+            RUN_TRY(enqueue_lsqr_cycle(R, d_b, p, k));
         }
         return PICCS_OK;
     }
     // data residual r = b - A x0 (also flags NaN/Inf in b)
-    LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->x, ctx->r,
-                                 bf16 ? FWD_RESID16 : FWD_RESID, d_b,
-                                 nullptr, &ctx->ks->nonfinite, st, SL(ctx)));
+    RUN_TRY(run_forward(R, bf16 ? FWD_RESID16 : FWD_RESID, [&](piccs_ctx *c) {
+        return fwd_job(c, c->x, c->r, d_b(c), nullptr, &c->ks->nonfinite);
+    }));
     for (int k = 0; k < p->n_outer; ++k) {
         // reweighting at the previous iterate (Eqs. 10-11)
-        int rc = enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx));
-        if (rc != PICCS_OK) return rc;
+        EACH(R) RUN_TRY(enqueue_weights(ctx, ctx->x, p, ctx->omega, ctx->c, SL(ctx)));
         // restart: g = c - D^T Omega D x, s = A^T r + g
         if (k == 0) {
-            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
-                                             ctx->s, 1, nullptr, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1, st, SL(ctx)));
+            EACH(R) LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
+                                                                     ctx->s, 1, nullptr, ctx->stream, SL(ctx)));
+            RUN_TRY(run_adjoint(R));
+            EACH(R) {
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(ctx->M, ctx->s, ctx->part_vec, ctx->stream, SL(ctx)));
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 1,
+                                                                       ctx->stream, SL(ctx)));
+            }
         } else {
-            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
-                                             ctx->s, 0, ctx->part_vol, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vol, ctx->n_part_vol, 1, st, SL(ctx)));
+            EACH(R) {
+                LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_restart(ctx->vd, ctx->x, ctx->omega, l2p, ctx->c, ctx->g,
+                                                                 ctx->s, 0, ctx->part_vol, ctx->stream, SL(ctx)));
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vol, ctx->n_part_vol, 1,
+                                                                       ctx->stream, SL(ctx)));
+            }
         }
         for (int it = 0; it < p->n_inner; ++it) {
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(M, ctx->s, ctx->p, ctx->ks, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t, ctx->part_vol, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_FORWARD, launch_forward(ctx->pg, ctx->cols, ctx->vr, ctx->cells, ctx->p, ctx->q, FWD_PLAIN,
-                                         nullptr, ctx->part_fwd, nullptr, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
-                                                ctx->part_vol, ctx->n_part_vol, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(M, N, ctx->x, ctx->p, ctx->g, ctx->t, ctx->s, ctx->r,
-                                          ctx->q, ctx->ks, st, SL(ctx)));
+            EACH(R) {
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_p_update(ctx->M, ctx->s, ctx->p, ctx->ks, ctx->stream, SL(ctx)));
+                LAUNCH(ctx, PICCS_KERNEL_REG, launch_reg_normal(ctx->vd, ctx->p, ctx->omega, l2p, ctx->t,
+                                                                ctx->part_vol, ctx->stream, SL(ctx)));
+            }
+            RUN_TRY(run_forward(R, FWD_PLAIN, [&](piccs_ctx *c) {
+                return fwd_job(c, c->p, c->q, nullptr, c->part_fwd, nullptr);
+            }));
+            EACH(R) {
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_delta(ctx->ks, ctx->part_fwd, ctx->n_part_fwd,
+                                                                       ctx->part_vol, ctx->n_part_vol, ctx->stream,
+                                                                       SL(ctx)));
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_x_update(ctx->M, ctx->N, ctx->x, ctx->p, ctx->g, ctx->t,
+                                                                 ctx->s, ctx->r, ctx->q, ctx->ks, ctx->stream,
+                                                                 SL(ctx)));
+            }
             // after the reconstruction's last step s = A^T r + g only feeds the
             // history, so its backprojection is skipped
             if (k == p->n_outer - 1 && it == p->n_inner - 1) break;
-            LAUNCH(ctx, PICCS_KERNEL_ADJOINT, launch_adjoint(ctx->pg, ctx->cols, ctx->vr, ctx->hit_ptr, ctx->hits, ctx->r, ctx->rs, ctx->s, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(M, ctx->s, ctx->part_vec, st, SL(ctx)));
-            LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0, st, SL(ctx)));
+            RUN_TRY(run_adjoint(R));
+            EACH(R) {
+                LAUNCH(ctx, PICCS_KERNEL_VECTOR, launch_norm2(ctx->M, ctx->s, ctx->part_vec, ctx->stream, SL(ctx)));
+                LAUNCH(ctx, PICCS_KERNEL_SCALAR, launch_finalize_gamma(ctx->ks, ctx->part_vec, ctx->n_part_vec, 0,
+                                                                       ctx->stream, SL(ctx)));
+            }
         }
     }
     return PICCS_OK;
+}
+
+}  // extern "C++"
+
+// one context, its data at d_b (allocates the re-orthogonalisation basis on
+// first use, which synchronises)
+static int enqueue_reconstruct(piccs_ctx *ctx, const float *d_b, const piccs_params *p,
+                               const float *d_x0, size_t x0_pitch)
+{
+    if (p->solver == PICCS_SOLVER_LSQR_REORTH) RUN_TRY(ensure_basis(ctx, p->n_inner, p->storage));
+    Run R{};
+    R.m[0] = ctx;
+    R.n = 1;
+    return enqueue_reconstruct(R, [d_b](piccs_ctx *) { return d_b; }, p, d_x0, x0_pitch);
 }
 
 static int check_reconstruct_args(piccs_ctx *ctx, const void *proj, const piccs_params *params,
@@ -928,11 +1077,10 @@ int piccs_unstage(piccs_ctx *ctx, int slot, float *vol, int to_host)
     return PICCS_OK;
 }
 
-int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph)
+// Validates and prepares one member of a staged run (BF16 rounding of FP32
+// staged data on its own stream, the re-orthogonalisation basis).
+static int prepare_staged(piccs_ctx *ctx, int nactive, const piccs_params *params)
 {
-    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
-    char why[256];
-    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(ctx, PICCS_EINVAL, "%s", why);
     if (nactive < 1 || nactive > ctx->nslot) return set_err(ctx, PICCS_EINVAL, "nactive %d out of range", nactive);
     if (params->x0_mode == PICCS_X0_USER) return set_err(ctx, PICCS_EINVAL, "staged runs start from the prior or zero");
     if (needs_prior(params) && !ctx->has_prior) return set_err(ctx, PICCS_EINVAL, "prior not set");
@@ -949,56 +1097,134 @@ int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, in
             ctx->staged16[b] = 1;
         }
     }
-    if (params->solver == PICCS_SOLVER_LSQR_REORTH) {  // allocate before any capture
-        int rc = ensure_basis(ctx, params->n_inner, params->storage);
-        if (rc != PICCS_OK) return rc;
+    if (params->solver == PICCS_SOLVER_LSQR_REORTH)  // allocate before any capture
+        RUN_TRY(ensure_basis(ctx, params->n_inner, params->storage));
+    return PICCS_OK;
+}
+
+// `after` waits for what has been enqueued on `before` so far
+static int stream_after(piccs_ctx *ctx, cudaStream_t before, cudaStream_t after)
+{
+    if (before == after) return PICCS_OK;
+    cudaEvent_t e = take_event(ctx);
+    if (!e) return set_err(ctx, PICCS_ECUDA, "cudaEventCreate failed");
+    cudaError_t err = cudaEventRecord(e, before);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(after, e, 0);
+    ctx->event_pool.push_back(e);  // reusable once the wait is enqueued
+    if (err != cudaSuccess) return set_err(ctx, PICCS_ECUDA, "stream ordering failed: %s", cudaGetErrorString(err));
+    return PICCS_OK;
+}
+
+int piccs_run_staged_group(piccs_ctx *const *ctxs, const int *nactive, int n, const piccs_params *params,
+                           int use_graph)
+{
+    if (!ctxs || !nactive || n < 1 || n > kMaxGroup)
+        return set_err(nullptr, PICCS_EINVAL, "group of %d contexts (1 .. %d)", n, kMaxGroup);
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return set_err(nullptr, PICCS_EINVAL, "ctxs[%d] is NULL", i);
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return set_err(ctxs[0], PICCS_EINVAL, "context %d appears twice", i);
+        if (ctxs[i]->device != ctxs[0]->device)
+            return set_err(ctxs[0], PICCS_EINVAL, "context %d is on another device", i);
     }
-    if (!use_graph || ctx->timing) return enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);
-    // one CUDA graph per (parameters, active slots): the launch sequence is
-    // fixed, every per-step scalar lives on the device
+    piccs_ctx *lead = ctxs[0];
+    char why[256];
+    if (check_params(params, why, sizeof why) != PICCS_OK) return set_err(lead, PICCS_EINVAL, "%s", why);
+    for (int i = 0; i < n; ++i) {
+        int rc = prepare_staged(ctxs[i], nactive[i], params);
+        if (rc != PICCS_OK) {
+            if (i > 0) set_err(lead, rc, "context %d: %s", i, ctxs[i]->err.c_str());
+            return rc;
+        }
+    }
+    Run R{};
+    R.n = n;
+    for (int i = 0; i < n; ++i) R.m[i] = ctxs[i];
+    auto staged = [](piccs_ctx *c) { return static_cast<const float *>(c->bstage); };
+    // every member's work on the lead's stream, after each member's staging
+    cudaStream_t saved[kMaxGroup];
+    for (int i = 0; i < n; ++i) saved[i] = ctxs[i]->stream;
+    for (int i = 1; i < n; ++i) RUN_TRY(stream_after(lead, saved[i], saved[0]));
+    auto on = [&](cudaStream_t st) {
+        for (int i = 0; i < n; ++i) ctxs[i]->stream = st;
+    };
+    auto restore = [&]() {
+        for (int i = 0; i < n; ++i) ctxs[i]->stream = saved[i];
+    };
+    auto finish = [&](int rc) {
+        restore();
+        // each member's unstaging copies follow the run
+        for (int i = 1; i < n && rc == PICCS_OK; ++i) rc = stream_after(lead, saved[0], saved[i]);
+        return rc;
+    };
+    bool timing = false;
+    for (int i = 0; i < n; ++i) timing |= ctxs[i]->timing;
+    if (!use_graph || timing) {
+        on(saved[0]);
+        return finish(enqueue_reconstruct(R, staged, params, nullptr, 0));
+    }
+    // one CUDA graph per (parameters, members, active slots, basis
+    // allocations): the launch sequence is fixed, every per-step scalar lives
+    // on the device; kept by the lead
     std::string key(reinterpret_cast<const char *>(params), sizeof *params);
-    key.append(reinterpret_cast<const char *>(&nactive), sizeof nactive);
-    auto it = ctx->graphs.find(key);
-    if (it == ctx->graphs.end()) {
-        long long before[PICCS_KERNEL_CLASSES], before_calls[PICCS_KERNEL_CLASSES];
-        std::memcpy(before, ctx->launches, sizeof before);
-        std::memcpy(before_calls, ctx->calls, sizeof before_calls);
-        if (!ctx->cap_stream)
-            CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < n; ++i) {
+        const long long id[3] = {ctxs[i]->uid, nactive[i], ctxs[i]->basis_gen};
+        key.append(reinterpret_cast<const char *>(id), sizeof id);
+    }
+    auto it = lead->graphs.find(key);
+    if (it == lead->graphs.end()) {
+        long long before[kMaxGroup][PICCS_KERNEL_CLASSES], before_calls[kMaxGroup][PICCS_KERNEL_CLASSES];
+        for (int i = 0; i < n; ++i) {
+            std::memcpy(before[i], ctxs[i]->launches, sizeof before[i]);
+            std::memcpy(before_calls[i], ctxs[i]->calls, sizeof before_calls[i]);
+        }
+        if (!lead->cap_stream)
+            CUDA_TRY(lead, cudaStreamCreateWithFlags(&lead->cap_stream, cudaStreamNonBlocking));
         // capture on the private stream (nothing runs during a capture), then
-        // launch the graph on the context's stream
-        CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaStream_t user = ctx->stream;
-        ctx->stream = ctx->cap_stream;
-        int rc = enqueue_reconstruct(ctx, ctx->bstage, params, nullptr, 0);
-        ctx->stream = user;
+        // launch the graph on the lead's stream
+        CUDA_TRY(lead, cudaStreamBeginCapture(lead->cap_stream, cudaStreamCaptureModeThreadLocal));
+        on(lead->cap_stream);
+        int rc = enqueue_reconstruct(R, staged, params, nullptr, 0);
+        restore();
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        cudaError_t e = cudaStreamEndCapture(lead->cap_stream, &graph);
         if (rc != PICCS_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return rc != PICCS_OK ? rc : set_err(ctx, PICCS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            return finish(rc != PICCS_OK ? rc
+                                         : set_err(lead, PICCS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e)));
         }
         cudaGraphExec_t exec = nullptr;
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return set_err(ctx, PICCS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess)
+            return finish(set_err(lead, PICCS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e)));
         piccs_ctx::GraphEntry ge;
         ge.exec = exec;
         for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
-            ge.launches[k] = ctx->launches[k] - before[k];
-            ge.calls[k] = ctx->calls[k] - before_calls[k];
-            ctx->launches[k] = before[k];  // counted when the graph runs
-            ctx->calls[k] = before_calls[k];
+            // counted on the lead when the graph runs
+            for (int i = 0; i < n; ++i) {
+                ge.launches[k] += ctxs[i]->launches[k] - before[i][k];
+                ge.calls[k] += ctxs[i]->calls[k] - before_calls[i][k];
+                ctxs[i]->launches[k] = before[i][k];
+                ctxs[i]->calls[k] = before_calls[i][k];
+            }
         }
-        it = ctx->graphs.emplace(key, ge).first;
+        it = lead->graphs.emplace(key, ge).first;
     }
-    CUDA_TRY(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
+    cudaError_t e = cudaGraphLaunch(it->second.exec, saved[0]);
+    if (e != cudaSuccess) return finish(set_err(lead, PICCS_ECUDA, "cudaGraphLaunch failed: %s", cudaGetErrorString(e)));
     for (int k = 0; k < PICCS_KERNEL_CLASSES; ++k) {
-        ctx->launches[k] += it->second.launches[k];
-        ctx->calls[k] += it->second.calls[k];
+        lead->launches[k] += it->second.launches[k];
+        lead->calls[k] += it->second.calls[k];
     }
-    ctx->graph_launches += 1;
-    return PICCS_OK;
+    lead->graph_launches += 1;
+    return finish(PICCS_OK);
+}
+
+int piccs_run_staged(piccs_ctx *ctx, int nactive, const piccs_params *params, int use_graph)
+{
+    if (!ctx) return set_err(nullptr, PICCS_EINVAL, "ctx is NULL");
+    return piccs_run_staged_group(&ctx, &nactive, 1, params, use_graph);
 }
 
 }  // extern "C"

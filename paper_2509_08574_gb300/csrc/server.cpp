@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -58,6 +59,8 @@ struct Session {
     std::vector<Request *> running;
     bool finished = false;  // set by the completion host function (under mu)
     long long last_used = 0;
+    long long unit = 0;     // issue unit of the running batch (shared by a group's sessions)
+    double unit_ms = 0.0;   // estimated device time per scan of that whole unit
 };
 
 struct PendingPatient {
@@ -232,65 +235,107 @@ bool same_params(const piccs_params &a, const piccs_params &b)
     return std::memcmp(&a, &b, sizeof a) == 0;
 }
 
-// Issues the next batch of session s; false if it has to wait for memory.
+// Issues the batches of sessions g[0..n) as one unit: one session's batch,
+// or (n > 1) a group -- sessions of different patients whose head requests
+// share parameters, run together by piccs_run_staged_group.  Sessions that
+// have to wait for memory are left out; false if none could be issued.
 // backlog: requests queued over all sessions.
-bool issue_batch(piccs_server *srv, Session &s, int backlog)
+bool issue_unit(piccs_server *srv, Session *const *g, int n, int backlog)
 {
-    Request *head = s.queue.front();
-    int rc = make_resident(srv, s, head->params);
-    if (rc == 1) return false;
-    std::vector<Request *> batch;
-    if (rc != PICCS_OK) {  // this request cannot run: fail it alone
-        s.queue.pop_front();
-        head->status = rc;
-        batch.push_back(head);
-        finish_requests(srv, batch, rc);
-        return true;
+    // make every member resident first (their queues are still full, so
+    // admitting one cannot evict another)
+    std::vector<Session *> ready;
+    bool issued = false;
+    for (int i = 0; i < n; ++i) {
+        Session &s = *g[i];
+        Request *head = s.queue.front();
+        const int rc = make_resident(srv, s, head->params);
+        if (rc == 1) continue;
+        if (rc != PICCS_OK) {  // this request cannot run: fail it alone
+            s.queue.pop_front();
+            head->status = rc;
+            std::vector<Request *> one{head};
+            finish_requests(srv, one, rc);
+            issued = true;
+            continue;
+        }
+        ready.push_back(&s);
     }
+    if (ready.empty()) return issued;
+    const piccs_params params = ready[0]->queue.front()->params;
     // A long scan gains little from sharing launches (the GPU is full either
     // way) while the first scan of a batch waits for the whole batch: long
     // scans are batched only to work off a deep backlog.
-    const int cap = head->est_ms < kGraphMs || backlog > 2 * srv->cfg.max_batch ? srv->cfg.max_batch : 1;
-    for (auto it = s.queue.begin(); it != s.queue.end() && (int)batch.size() < cap;) {
-        if (same_params((*it)->params, head->params)) {
-            batch.push_back(*it);
-            it = s.queue.erase(it);
-        } else {
-            ++it;
+    std::vector<std::vector<Request *>> batches(ready.size());
+    bool graph = srv->cfg.use_graphs != 0;
+    double unit_ms = 0.0;
+    int rc = PICCS_OK;
+    const auto now = Clock::now();
+    for (size_t m = 0; m < ready.size(); ++m) {
+        Session &s = *ready[m];
+        Request *head = s.queue.front();
+        const int cap = head->est_ms < kGraphMs || backlog > 2 * srv->cfg.max_batch ? srv->cfg.max_batch : 1;
+        for (auto it = s.queue.begin(); it != s.queue.end() && (int)batches[m].size() < cap;) {
+            if (same_params((*it)->params, params)) {
+                batches[m].push_back(*it);
+                it = s.queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        graph = graph && head->est_ms < kGraphMs;
+        unit_ms += head->est_ms;
+        const int nb = (int)batches[m].size();
+        for (int i = 0; i < nb; ++i) {
+            batches[m][i]->t_issue = now;
+            batches[m][i]->batch = nb;
+            if (rc == PICCS_OK)
+                rc = params.storage == PICCS_STORAGE_BF16
+                         ? piccs_stage_bf16(s.ctx, i, batches[m][i]->h_proj, 1)
+                         : piccs_stage(s.ctx, i, static_cast<const float *>(batches[m][i]->h_proj), 1);
         }
     }
-    const int n = (int)batch.size();
-    const auto now = Clock::now();
-    for (int i = 0; i < n; ++i) {
-        batch[i]->t_issue = now;
-        batch[i]->batch = n;
-        if (rc == PICCS_OK)
-            rc = head->params.storage == PICCS_STORAGE_BF16
-                     ? piccs_stage_bf16(s.ctx, i, batch[i]->h_proj, 1)
-                     : piccs_stage(s.ctx, i, static_cast<const float *>(batch[i]->h_proj), 1);
+    const int nm = (int)ready.size();
+    piccs_ctx *ctxs[8];
+    int nact[8];
+    for (int m = 0; m < nm; ++m) {
+        ctxs[m] = ready[m]->ctx;
+        nact[m] = (int)batches[m].size();
     }
-    const bool graph = srv->cfg.use_graphs && head->est_ms < kGraphMs;
-    if (rc == PICCS_OK) rc = piccs_run_staged(s.ctx, n, &head->params, graph);
-    for (int i = 0; i < n && rc == PICCS_OK; ++i) rc = piccs_unstage(s.ctx, i, batch[i]->h_out, 1);
-    if (rc == PICCS_OK) {
-        DoneArg *a = new (std::nothrow) DoneArg{srv, &s};
-        if (!a || cudaLaunchHostFunc(s.stream, batch_done, a) != cudaSuccess) {
+    if (rc == PICCS_OK) rc = piccs_run_staged_group(ctxs, nact, nm, &params, graph);
+    for (int m = 0; m < nm && rc == PICCS_OK; ++m)
+        for (int i = 0; i < nact[m] && rc == PICCS_OK; ++i)
+            rc = piccs_unstage(ready[m]->ctx, i, batches[m][i]->h_out, 1);
+    for (int m = 0; m < nm && rc == PICCS_OK; ++m) {
+        DoneArg *a = new (std::nothrow) DoneArg{srv, ready[m]};
+        if (!a || cudaLaunchHostFunc(ready[m]->stream, batch_done, a) != cudaSuccess) {
             delete a;
             cudaGetLastError();
             rc = PICCS_ECUDA;
         }
     }
-    if (rc != PICCS_OK) {  // the session's state is unknown: drop it, it is re-created on demand
-        if (s.stream) cudaStreamSynchronize(s.stream);
-        evict(srv, s);
-        finish_requests(srv, batch, rc);
+    if (rc != PICCS_OK) {  // the sessions' state is unknown: drop them, they are re-created on demand
+        for (int m = 0; m < nm; ++m) {
+            Session &s = *ready[m];
+            if (s.stream) cudaStreamSynchronize(s.stream);
+            s.running.clear();
+            evict(srv, s);
+            finish_requests(srv, batches[m], rc);
+        }
         return true;
     }
-    s.running = std::move(batch);
-    s.last_used = ++srv->tick;
+    const long long unit = ++srv->tick;
+    for (int m = 0; m < nm; ++m) {
+        Session &s = *ready[m];
+        s.running = std::move(batches[m]);
+        s.last_used = unit;
+        s.unit = unit;
+        s.unit_ms = unit_ms;
+    }
     std::lock_guard<std::mutex> lk(srv->mu);
-    srv->st.batches += 1;
+    srv->st.batches += nm;
     if (graph) srv->st.graph_replays += 1;
+    if (nm > 1) srv->st.group_runs += 1;
     return true;
 }
 
@@ -345,13 +390,17 @@ void worker_main(piccs_server *srv)
         // issue: highest response ratio (waited + estimated run) / estimated
         // run first -- short scans go ahead of long ones, and a long scan's
         // ratio grows while it waits, so none waits without bound
+        // in flight: issue units (a group's sessions share one)
         int running = 0;
         bool big_running = false;
-        for (auto &kv : srv->sessions)
-            if (!kv.second.running.empty()) {
-                running += 1;
-                big_running |= kv.second.running.front()->est_ms >= kOverlapMs;
-            }
+        {
+            std::set<long long> units;
+            for (auto &kv : srv->sessions)
+                if (!kv.second.running.empty() && units.insert(kv.second.unit).second) {
+                    running += 1;
+                    big_running |= kv.second.unit_ms >= kOverlapMs;
+                }
+        }
         int backlog = 0;
         for (auto &kv : srv->sessions) backlog += (int)kv.second.queue.size();
         const bool by_ratio = srv->cfg.order == PICCS_ORDER_RESPONSE_RATIO ||
@@ -374,26 +423,56 @@ void worker_main(piccs_server *srv)
                 }
             }
             if (!best) break;
+            // a short head scan takes other idle sessions whose head requests
+            // share its parameters along, in issue order, as one group
+            std::vector<Session *> unit{best};
+            const Request *bh = best->queue.front();
+            if (srv->cfg.max_group > 1 && bh->est_ms < kGraphMs) {
+                std::vector<std::pair<double, Session *>> cand;
+                for (auto &kv : srv->sessions) {
+                    Session &o = kv.second;
+                    if (&o == best || !o.running.empty() || o.queue.empty()) continue;
+                    const Request *h = o.queue.front();
+                    if (h->est_ms >= kGraphMs || !same_params(h->params, bh->params)) continue;
+                    cand.push_back({!by_ratio ? -(double)h->id
+                                              : (ms_between(h->t_submit, now) + h->est_ms) / h->est_ms,
+                                    &o});
+                }
+                std::stable_sort(cand.begin(), cand.end(),
+                                 [](const std::pair<double, Session *> &a, const std::pair<double, Session *> &b) {
+                                     return a.first > b.first;
+                                 });
+                for (auto &c : cand) {
+                    if ((int)unit.size() >= srv->cfg.max_group) break;
+                    unit.push_back(c.second);
+                }
+            }
+            double unit_ms = 0.0;
+            for (Session *u : unit) unit_ms += u->queue.front()->est_ms;
             // batches overlap only while every one of them is small; the order
             // is kept: nothing overtakes a large scan that is next
-            if (running > 0 && (big_running || best->queue.front()->est_ms >= kOverlapMs)) break;
-            if (issue_batch(srv, *best, backlog)) {
+            if (running > 0 && (big_running || unit_ms >= kOverlapMs)) break;
+            if (issue_unit(srv, unit.data(), (int)unit.size(), backlog)) {
                 progress = true;
-                if (!best->running.empty()) {
-                    running += 1;
-                    big_running |= best->running.front()->est_ms >= kOverlapMs;
-                }
+                bool any = false;
+                for (Session *u : unit)
+                    if (!u->running.empty()) {
+                        any = true;
+                        big_running |= u->unit_ms >= kOverlapMs;
+                    }
+                if (any) running += 1;
             } else {
                 // wait for memory: try sessions that are already resident
                 for (auto &kv : srv->sessions) {
                     Session &s = kv.second;
                     if (&s == best || !s.running.empty() || s.queue.empty() || !s.ctx) continue;
                     if (running > 0 && (big_running || s.queue.front()->est_ms >= kOverlapMs)) continue;
-                    if (issue_batch(srv, s, backlog)) {
+                    Session *one = &s;
+                    if (issue_unit(srv, &one, 1, backlog)) {
                         progress = true;
                         if (!s.running.empty()) {
                             running += 1;
-                            big_running |= s.running.front()->est_ms >= kOverlapMs;
+                            big_running |= s.unit_ms >= kOverlapMs;
                         }
                         break;
                     }
@@ -443,6 +522,7 @@ int piccs_server_create(piccs_server **out, const piccs_server_config *cfg)
     if (cfg->max_running < 1) return fail(nullptr, PICCS_EINVAL, "max_running must be >= 1");
     if (cfg->order < PICCS_ORDER_RESPONSE_RATIO || cfg->order > PICCS_ORDER_ADAPTIVE)
         return fail(nullptr, PICCS_EINVAL, "unknown order %d", cfg->order);
+    if (cfg->max_group < 0 || cfg->max_group > 8) return fail(nullptr, PICCS_EINVAL, "max_group must be in [0, 8]");
     piccs_server *srv = new (std::nothrow) piccs_server();
     if (!srv) return fail(nullptr, PICCS_ENOMEM, "host allocation failed");
     srv->cfg = *cfg;

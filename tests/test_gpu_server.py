@@ -1,8 +1,9 @@
 """The request server on the GPU: repeated scans of several patients (each
 with its own geometry and prior) arrive interleaved; every result must equal
 the same scan reconstructed alone through piccs_reconstruct, bit for bit,
-whether it ran in a batch, next to other patients' batches, from a replayed
-CUDA graph, or after its session was evicted and made resident again."""
+whether it ran in a batch, next to other patients' batches, in a group with
+other patients' scans of other sizes, from a replayed CUDA graph, or after
+its session was evicted and made resident again."""
 import numpy as np
 import pytest
 
@@ -105,6 +106,32 @@ def test_queued_scans_are_batched(pk, patients):
     assert s["batches"] < 9
     ref = _alone(pk, g, prior, scans[1], params)
     assert torch.equal(torch.from_numpy(tickets[5][1]), ref)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_patients_of_different_sizes_run_as_groups(pk, patients, graphs):
+    """Scans of three patients with different geometries and the same
+    parameters, queued behind one batch in flight: the next issue takes
+    all three sessions as one group (shared projector launches); every
+    result equals the scan reconstructed alone, bit for bit."""
+    params = pk.make_params(**PARAMS[0])
+    with pk.Server(max_batch=2, max_running=1, use_graphs=graphs, max_group=4) as srv:
+        for k, (g, prior, _) in enumerate(patients):
+            srv.add_patient(k, g, prior)
+        tickets = []
+        for i in range(3):
+            for k, (g, _, scans) in enumerate(patients):
+                out = torch.empty(g.vol_shape(), dtype=torch.float32).pin_memory()
+                t, out = srv.submit(k, scans[i], params, out=out)
+                tickets.append((k, i, t, out))
+        stats = [srv.wait(t) for _, _, t, _ in tickets]
+        s = srv.stats()
+    assert all(st["status"] == 0 for st in stats), stats
+    assert s["group_runs"] >= 1, s
+    assert s["completed"] == len(tickets)
+    for (k, i, _, out) in tickets:
+        g, prior, scans = patients[k]
+        assert torch.equal(out, _alone(pk, g, prior, scans[i], params)), (k, i)
 
 
 def test_admission_evicts_idle_sessions(pk, patients):

@@ -14,7 +14,8 @@ def pk():
 
 
 def test_config_is_checked(pk):
-    for kw in (dict(max_batch=0), dict(max_batch=65), dict(max_running=0), dict(order=3)):
+    for kw in (dict(max_batch=0), dict(max_batch=65), dict(max_running=0), dict(order=3),
+               dict(max_group=-1), dict(max_group=9)):
         with pytest.raises(pk.PiccsError) as e:
             pk.Server(hbm_budget=1 << 30, **kw)
         assert e.value.code == pk.PICCS_EINVAL
