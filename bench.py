@@ -235,6 +235,19 @@ class ClockSampler:
         return parse_clock_csv(text)
 
 
+def adjoint_kernel_names(g):
+    """The two kernels of one backprojection on geometry g, by the library's
+    choice: the prefix-sum gather for even nv and nz, at most one z crossing
+    of a row per xy cell, nz <= 512 and at least 2.5 detector rows per voxel
+    layer; the candidate gather otherwise."""
+    vmax = 0.5 * (g.nv - 1) * g.dv
+    multi = vmax > 0 and g.vz * g.dsd <= 1.01 * np.hypot(g.vx, g.vy) * vmax
+    rows_per_layer = g.vz * g.dsd / (g.dso * g.dv)
+    if g.nv % 2 == 0 and g.nz % 2 == 0 and not multi and g.nz <= 512 and rows_per_layer >= 2.5:
+        return "ray_prefix_kernel+adj_prefix_kernel"
+    return "scale_rays_kernel+adj_gather_kernel"
+
+
 def projector_ms_per_application(prof, batch):
     """Device ms of one application of A and of A^T per scan, from a library
     profile: each class's summed time over its operator calls (not its kernel
@@ -457,7 +470,7 @@ def run_ours(args):
     alg_bytes = 4.0 * (nz_ + g.M + g.N)
     achieved = alg_bytes / (per[dom] * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    kernel_names = {"forward": "fwd_kernel", "adjoint": "scale_rays_kernel+adj_gather_kernel"}
+    kernel_names = {"forward": "fwd_kernel", "adjoint": adjoint_kernel_names(g)}
 
     line = {
         "metric": METRIC if args.workload == "c2_needle" else

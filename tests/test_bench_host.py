@@ -162,3 +162,12 @@ def test_both_arms_state_the_same_config():
     assert cfg == bench.bench_config(scan, A)
     assert cfg["noise_draws"] == 10 and cfg["batch"] == 1 and cfg["storage"] == "f32"
     assert "workspace" not in cfg["l2"]
+
+
+def test_adjoint_kernel_label_follows_the_gather_choice():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.adjoint_kernel_names(bench.workload("c2_needle").geometry).startswith("scale_rays")
+    assert bench.adjoint_kernel_names(bench.workload("c3_sphere_growth").geometry).startswith("scale_rays")
+    assert bench.adjoint_kernel_names(bench.workload("c5_carm").geometry).startswith("ray_prefix")
