@@ -373,7 +373,10 @@ __device__ __forceinline__ void adj_gather_block(const ProjGeom &G, const ColPar
     for (int q = 0; q < L; ++q) {
         const int p = pb + q * kGatherThreads;
         pok[q] = p < nlp;
-        zlo[q] = (float)(G.nz - 1 - p) - G.halfnz;  // lower plane of the upper layer (>= -0.5)
+        // lower plane of the upper layer (>= -0.5); a thread beyond the last
+        // pair gets a plane far above every ray, which puts its lower candidate
+        // bound above every row (its sums are not written in any case)
+        zlo[q] = pok[q] ? (float)(G.nz - 1 - p) - G.halfnz : 1e20f;
         accu[q] = 0.f;
         accd[q] = 0.f;
     }
@@ -392,8 +395,12 @@ __device__ __forceinline__ void adj_gather_block(const ProjGeom &G, const ColPar
             const float sa = __int_as_float(e.y), sb = __int_as_float(e.z);
             const float4 cz = __ldg(reinterpret_cast<const float4 *>(cols + (long long)j * G.nu + iu) + 1);
             const float s0 = cz.x, KD = cz.y, rKD = cz.w;
-            // candidate bounds only: the rows are then checked exactly
-            const float rGa = rcp_approx((s0 + sa) * rKD), rGb = rcp_approx((s0 + sb) * rKD);
+            // detector rows per unit of plane coordinate at sa and at sb,
+            // 1 / (G(s) dv): candidate bounds only (rounded as often as
+            // zl / G(s) / dv would be, well inside the 1e-3-row margin up to
+            // thousands of rows), the rows are then checked exactly
+            const float rGa = rcp_approx((s0 + sa) * rKD) * G.rdv;
+            const float rGb = rcp_approx((s0 + sb) * rKD) * G.rdv;
             const int roff = EVEN ? (j * G.nu + iu) * (G.nv >> 1)  // pair index of row nv / 2
                                   : (int)((long long)j * G.sj + (long long)iu * G.su);  // N < 2^31
             hc_a[threadIdx.x] = make_float4(sa, sb, s0, KD);
@@ -413,11 +420,14 @@ __device__ __forceinline__ void adj_gather_block(const ProjGeom &G, const ColPar
                 const float zl = zlo[q], zh = zl + 1.f;
                 // G grows with s, so 1/G(sa) >= 1/G(sb); upper layers have zl >= 0
                 // except the middle layer of an odd nz (zl = -0.5)
-                const float vlo = zl * (zl >= 0.f ? rGb : rGa), vhi = zh * rGa;
-                int ilo = __float2int_ru(fmaf(vlo, G.rdv, G.cv - 1e-3f));
-                int ihi = __float2int_rd(fmaf(vhi, G.rdv, G.cv + 1e-3f));
-                ilo = max(ilo, EVEN ? (G.nv >> 1) : 0);
-                ihi = pok[q] ? min(ihi, nvm1) : -1;
+                // Candidate rows ilo .. ihi, held in 0 (EVEN: nv / 2) .. nv - 1
+                // whatever the bounds' values: the conversions saturate, and ilo
+                // is clamped to nv at most, so that ilo + 3 cannot overflow.
+                const int ilo = min(max(__float2int_ru(fmaf(zl, EVEN || zl >= 0.f ? rGb : rGa,
+                                                            G.cv - 1e-3f)),
+                                        EVEN ? (G.nv >> 1) : 0),
+                                    G.nv);
+                const int ihi = min(__float2int_rd(fmaf(zh, rGa, G.cv + 1e-3f)), nvm1);
                 // only a layer touching z = 0 can hold the middle row of an odd nv
                 // (v = 0), which is its own mirror and belongs to the upper layer
                 const bool mid = zl < 1.f && (nvm1 & 1) == 0;
