@@ -154,8 +154,12 @@ typedef struct piccs_ctx piccs_ctx;
  * checks device memory for the reconstruction workspace (PICCS_ENOMEM before
  * any allocation), allocates the workspace on the current device and
  * uploads the per-view ray tables.  cuda_stream is a cudaStream_t (NULL =
- * legacy default stream).  Synchronises.  Paper: Sec. 3 (one geometry per
- * scanning procedure, repeated scans of the same patient). */
+ * legacy default stream).  Synchronises.  The forward projector's walk is
+ * chosen here: for a volume larger than the device's L2 it loads the ray's
+ * cell table one entry ahead (the same sums); the environment variable
+ * PICCS_FORWARD_AHEAD=0 or 1, read at creation, overrides that choice.
+ * Paper: Sec. 3 (one geometry per scanning procedure, repeated scans of the
+ * same patient). */
 int piccs_create(piccs_ctx **out, const piccs_geometry *geometry, void *cuda_stream);
 
 /* Create a context that reconstructs `batch` scans of the same geometry

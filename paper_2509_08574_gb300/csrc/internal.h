@@ -43,6 +43,7 @@ struct ProjGeom {
     float rdv, cv;          // 1 / dv and (nv - 1) / 2: row index of height v = v * rdv + cv
     int sv32;               // sv as a 32-bit stride (1 or nu)
     int multi;              // a cell can hold more than one z crossing of a row
+    int ahead;              // the forward walk loads the cell table one entry early
     float rows_per_layer;   // detector rows one voxel layer spans at the isocentre
 };
 

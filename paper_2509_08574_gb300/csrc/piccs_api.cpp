@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <map>
@@ -378,6 +379,17 @@ int piccs_create_batched(piccs_ctx **out, const piccs_geometry *geometry, int ba
         const double diag = std::sqrt(g.vx * g.vx + g.vy * g.vy);
         ctx->pg.multi = vmax > 0.0 && g.vz * g.dsd <= 1.01 * diag * vmax ? 1 : 0;
         ctx->pg.rows_per_layer = (float)(g.vz * g.dsd / (g.dso * g.dv));
+        // A volume larger than the L2 makes the walk's cell-table loads miss:
+        // the forward then loads the table one entry ahead (the same sums).
+        // PICCS_FORWARD_AHEAD=0/1 overrides the choice (tuning and tests).
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            l2 = 0;
+        }
+        ctx->pg.ahead = l2 > 0 && (double)ctx->M * sizeof(float) > (double)l2 ? 1 : 0;
+        if (const char *ov = std::getenv("PICCS_FORWARD_AHEAD"))
+            if (ov[0] == '0' || ov[0] == '1') ctx->pg.ahead = ov[0] - '0';
     }
     ctx->vd = VolDims{g.nx, g.ny, g.nz};
 

@@ -3,8 +3,9 @@ every product with A and with A^T is one launch for all of them, every other
 kernel runs per context, and each result must equal the same context's
 staged run alone, bit for bit -- whatever the mix of projector paths (the
 even-size and the general candidate gather, the prefix-sum gather, the
-multi-crossing forward), the solver, the storage, the batch slots in use, and
-with or without a captured CUDA graph."""
+multi-crossing forward and the one that reads its cell table ahead), the
+solver, the storage, the batch slots in use, and with or without a captured
+CUDA graph."""
 import numpy as np
 import pytest
 
@@ -69,8 +70,19 @@ def _unstage(ctx, g, nactive):
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("pi", range(len(PARAMS)))
 def test_group_equals_each_context_alone(pk, members, pi, graph):
-    params = pk.make_params(0.5, 0.5, 1e-2, **PARAMS[pi])
-    nactive = [2, 1, 2, 1]
+    _check_group(pk, members, [2, 1, 2, 1], pk.make_params(0.5, 0.5, 1e-2, **PARAMS[pi]), graph)
+
+
+def test_group_with_the_ahead_walk_equals_each_context_alone(pk, members, monkeypatch):
+    """Every member created with the forward walk that reads the cell table
+    one entry ahead (without the multi-crossing geometry, whose walk a group
+    would take), so that the group launches take that walk too."""
+    monkeypatch.setenv("PICCS_FORWARD_AHEAD", "1")
+    for pi in range(len(PARAMS)):
+        _check_group(pk, members[:3], [2, 1, 2], pk.make_params(0.5, 0.5, 1e-2, **PARAMS[pi]), False)
+
+
+def _check_group(pk, members, nactive, params, graph):
     ctxs = [pk.Context(g, batch=2) for g, _, _ in members]
     try:
         for c, (g, prior, scans), na in zip(ctxs, members, nactive):

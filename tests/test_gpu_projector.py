@@ -92,6 +92,48 @@ def test_forward_matches_oracle(pk, name):
     assert np.all(y[miss] == 0)
 
 
+@pytest.fixture
+def ahead(monkeypatch):
+    """Chooses the forward walk of the contexts created while it is in effect
+    (PICCS_FORWARD_AHEAD; by default the library loads the cell table one
+    entry ahead only for volumes larger than the L2)."""
+    def set_walk(on):
+        monkeypatch.setenv("PICCS_FORWARD_AHEAD", "1" if on else "0")
+    return set_walk
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_forward_walk_ahead_is_bitwise_the_same(pk, name, ahead):
+    """The walk that reads the cell table one entry ahead gives the plain
+    walk's sums bit for bit (the multi-crossing geometry keeps its own walk)."""
+    g = GEOMS[name]()
+    x = _dev(_phantom_volume(g) if g.M > 50000 else P.random_volume(g, 2))
+    ys = []
+    for on in (False, True):
+        ahead(on)
+        with pk.Context(g) as ctx:
+            ys.append(ctx.forward(x).clone())
+    assert torch.equal(ys[0], ys[1])
+
+
+@pytest.mark.parametrize("solver,storage", [(0, 0), (1, 0), (2, 1)])
+def test_reconstruction_with_the_ahead_walk_is_bitwise_the_same(pk, solver, storage, ahead):
+    """The same through the reconstruction's forward variants: the residual
+    with its norm (CGLS, FP32 and BF16 data) and the LSQR u-step."""
+    scan = P.c1_small()
+    g = scan.geometry
+    b, xp = _dev(scan.measured()), _dev(scan.prior_volume(ss=1))
+    params = pk.make_params(0.5, 0.5, scan.tau, 2, 3, solver=solver, storage=storage)
+    xs = []
+    for on in (False, True):
+        ahead(on)
+        with pk.Context(g) as ctx:
+            ctx.set_prior(xp)
+            xs.append(ctx.reconstruct(b, params).clone())
+            assert ctx.report().status == 0
+    assert torch.equal(xs[0], xs[1])
+
+
 @pytest.mark.parametrize("name", list(GEOMS))
 def test_adjoint_matches_oracle(pk, name):
     g = GEOMS[name]()
