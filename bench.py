@@ -8,7 +8,8 @@ pixels (0.8 mm) over a 200 degree short scan, with every step of the path
 work) in this repository's CUDA kernels, inputs resident in HBM.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.  Under torchrun every rank
+instead: its whole reconstruction where that takes at most a minute (the 64^3
+workload), else a bounded sample of the same workload.  Under torchrun every rank
 runs an independent replica on its own GPU (the path has no exchange step).
 
 Other measurements: `--solver lsqr|lsqr_reorth` (the inner solver),
@@ -41,6 +42,7 @@ import phantoms as P  # noqa: E402
 METRIC = "PICCS-Krylov recon ms/scan p50 at 256^3 (90 views of 512^2, 30 its)"
 UNIT = "ms/scan"
 L2_FLUSH_BYTES = 256 << 20
+L2_BYTES = 129 * 10**6  # GB300's L2 (129 MB)
 SOLVERS = {"cgls": (0, "CGLS"), "lsqr": (1, "LSQR"), "lsqr_reorth": (2, "re-orthogonalised LSQR")}
 
 
@@ -95,9 +97,20 @@ def workload_config(scan, solver="cgls"):
         "volume": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.nu, g.nv],
         "iterations": scan.iterations, "alpha": scan.alpha, "lambda": scan.lam, "tau": scan.tau,
         "projection_layout": "view,u,v (v fastest)",
-        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); working set larger than L2",
+        "l2": l2_note(g),
         "parallelism": "replicas (one independent reconstruction per GPU)",
     }
+
+
+def l2_note(g):
+    """How the L2 is kept from serving one step's inputs to the next: always
+    a flush; whether the step's vectors alone (nine volume-sized and five
+    projection-sized FP32 arrays) would exceed the L2 anyway is stated."""
+    work = 4 * (9 * g.nx * g.ny * g.nz + 5 * g.n_views * g.nu * g.nv)
+    note = f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); "
+    if work > L2_BYTES:
+        return note + "working set larger than L2"
+    return note + "working set smaller than L2 (the flush evicts it)"
 
 
 def bench_config(scan, args):
@@ -135,9 +148,10 @@ def code_digest(path):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
-def traffic_record(kernel):
-    """Per-launch DRAM traffic from a committed ncu summary, valid only while
-    the projector code is unchanged since the counters were taken."""
+def traffic_record(kernel, workload):
+    """Per-launch DRAM traffic from a committed ncu summary, valid only for
+    the workload it was taken on and while the projector code is unchanged
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "projector_traffic.json")
     src = os.path.join(ROOT, "paper_2509_08574_gb300", "csrc", "kernels_project.cu")
     try:
@@ -146,7 +160,7 @@ def traffic_record(kernel):
         h = code_digest(src)
     except OSError:
         return None
-    if rec.get("code_sha256") != h:
+    if rec.get("code_sha256") != h or rec.get("bench_workload") != workload:
         return None
     total = 0.0
     for name in kernel.split("+"):
@@ -267,6 +281,13 @@ def pctl(xs, q):
 # --------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
+def metric_name(args, scan):
+    """The headline metric on the 256^3 workload, else the workload's own."""
+    if args.workload == "c2_needle":
+        return METRIC
+    return f"PICCS-Krylov recon ms/scan p50, {scan.name} ({scan.iterations} its)"
+
+
 def oracle_sample(scan, b, xp):
     """Times the FP64 oracle on a bounded sample of the workload: A and A^T on
     one view in ten, plus one pass of the regularisation blocks over the full
@@ -300,6 +321,38 @@ def oracle_sample(scan, b, xp):
     return per_scan_s * 1e3, cores, sample, t3 - t0
 
 
+# a whole oracle reconstruction is timed instead of the sample when the
+# sample's estimate of it is at most this long
+ORACLE_WHOLE_MAX_S = 60.0
+
+
+def oracle_whole(scan, b, xp, solver=0):
+    """Times the FP64 oracle's whole reconstruction of the workload: the same
+    projections, prior, parameters and solver as the GPU arm, end to end."""
+    import oracle as O
+
+    g = scan.geometry
+    x64 = xp.astype(np.float64)
+    t0 = time.perf_counter()
+    O.irn(g, np.ascontiguousarray(b, dtype=np.float64), x64, x64, scan.alpha, scan.lam, scan.tau,
+          scan.n_outer, scan.n_inner, solver=solver)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    name = next(v[1] for v in SOLVERS.values() if v[0] == solver)
+    sample = (f"the whole reconstruction, {scan.n_outer}x{scan.n_inner} {name} iterations on the "
+              f"{g.nx}x{g.ny}x{g.nz} workload ({dt:.1f} s)")
+    return dt * 1e3, cores, sample, dt
+
+
+def oracle_baseline(scan, b, xp, solver=0):
+    """The oracle's time per scan: its whole reconstruction when the sample
+    estimates that at ORACLE_WHOLE_MAX_S or less, else the sample's estimate."""
+    est = oracle_sample(scan, b, xp)
+    if est[0] <= ORACLE_WHOLE_MAX_S * 1e3:
+        return oracle_whole(scan, b, xp, solver)
+    return est
+
+
 def oracle_sample_1thread(scan, b, xp):
     """The oracle's projector pair on one thread, on one view: ms per scan
     extrapolated like oracle_sample (the regularisation pass is left out; it is
@@ -323,16 +376,17 @@ def run_reference(args):
     scan = workload(args.workload)
     b = scan.measured()
     xp = scan.prior_volume(ss=1)
+    solver = SOLVERS[args.solver][0]
     for _ in range(args.warmup):
-        oracle_sample(scan, b, xp)
+        oracle_baseline(scan, b, xp, solver)
     vals = []
     cores = sample = None
     for _ in range(args.steps):
-        v, cores, sample, _ = oracle_sample(scan, b, xp)
+        v, cores, sample, _ = oracle_baseline(scan, b, xp, solver)
         vals.append(v)
     value = pctl(vals, 50)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "impl": "reference", "metric": metric_name(args, scan), "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -473,8 +527,7 @@ def run_ours(args):
     kernel_names = {"forward": "fwd_kernel", "adjoint": adjoint_kernel_names(g)}
 
     line = {
-        "metric": METRIC if args.workload == "c2_needle" else
-                  f"PICCS-Krylov recon ms/scan p50, {scan.name} ({scan.iterations} its)",
+        "metric": metric_name(args, scan),
         # whole job: every rank reconstructs B scans per step, so the job's time
         # per scan is the (slowest rank's) step time over all ranks' scans
         "value": p50 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -496,7 +549,7 @@ def run_ours(args):
                       "adj_gups": nz_ / (per["adjoint"] * 1e-3) / 1e9},
         "roofline": {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_record(kernel_names[dom]),
+                     "frac": achieved / peak, "traffic": traffic_record(kernel_names[dom], args.workload),
                      "algorithmic_bytes_per_launch": alg_bytes},
         "clocks": clk,
         "wall_s_timed_region": t_wall, "input_generation_s": t_in,
@@ -526,7 +579,7 @@ def run_ours(args):
     if args.workload in GPU_SYNTH:
         line["data"] = "synthetic (phantom voxelised on the GPU, projected by this projector, Poisson noise)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline and b_np is not None:
-        v, cores, sample, _ = oracle_sample(scan, b_np, xp_np)
+        v, cores, sample, _ = oracle_baseline(scan, b_np, xp_np, SOLVERS[args.solver][0])
         v1, dt1 = oracle_sample_1thread(scan, b_np, xp_np)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample,

@@ -1,6 +1,9 @@
 """Host-side logic of bench.py without a GPU: the max-over-ranks timing
 reduction of the multi-GPU (replica) path on two gloo ranks, the reference
-arm's behaviour on ranks other than 0, and the clock-sample parser."""
+arm's behaviour on ranks other than 0, the clock-sample parser, the per-
+application projector accounting, the choice between the oracle's whole
+reconstruction and its sample, and which workload the DRAM record and the
+L2 note describe."""
 import os
 import socket
 import subprocess
@@ -171,3 +174,63 @@ def test_adjoint_kernel_label_follows_the_gather_choice():
     assert bench.adjoint_kernel_names(bench.workload("c2_needle").geometry).startswith("scale_rays")
     assert bench.adjoint_kernel_names(bench.workload("c3_sphere_growth").geometry).startswith("scale_rays")
     assert bench.adjoint_kernel_names(bench.workload("c5_carm").geometry).startswith("ray_prefix")
+
+
+def test_oracle_baseline_times_the_whole_reconstruction_when_it_is_short(monkeypatch):
+    """The oracle's time per scan is its whole reconstruction where the
+    sample estimates at most a minute for it, else the sample's estimate;
+    the whole run gets the arm's solver."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    calls = []
+    monkeypatch.setattr(bench, "oracle_whole",
+                        lambda scan, b, xp, solver=0: calls.append(solver) or (5.0, 1, "whole", 0.005))
+    for est_ms, whole in ((1e3, True), (bench.ORACLE_WHOLE_MAX_S * 1e3, True), (5.6e5, False)):
+        monkeypatch.setattr(bench, "oracle_sample", lambda scan, b, xp, e=est_ms: (e, 1, "sample", 1.0))
+        calls.clear()
+        got = bench.oracle_baseline(None, None, None, solver=2)
+        assert (got[2] == "whole") == whole and calls == ([2] if whole else [])
+        assert got[0] == (5.0 if whole else est_ms)
+
+
+def test_metric_names_the_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        workload = "c2_needle"
+
+    assert bench.metric_name(A, bench.workload("c2_needle")) == bench.METRIC
+    A.workload = "c1_small"
+    scan = bench.workload("c1_small")
+    m = bench.metric_name(A, scan)
+    assert m != bench.METRIC and scan.name in m and f"({scan.iterations} its)" in m
+
+
+def test_traffic_record_is_the_workloads_own():
+    """The committed DRAM counters describe one workload's launches: another
+    workload (or a changed projector source) reports no traffic."""
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "projector_traffic.json")) as f:
+        rec = json.load(f)
+    w = rec["bench_workload"]
+    others = [k for k in bench.WORKLOADS if k != w]
+    src = os.path.join(ROOT, "paper_2509_08574_gb300", "csrc", "kernels_project.cu")
+    current = rec["code_sha256"] == bench.code_digest(src)
+    for name in rec["kernels"]:
+        assert (bench.traffic_record(name, w) is not None) == current
+        for o in others:
+            assert bench.traffic_record(name, o) is None
+
+
+def test_l2_note_follows_the_working_set():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert "smaller than L2" in bench.l2_note(bench.workload("c1_small").geometry)
+    assert "larger than L2" in bench.l2_note(bench.workload("c2_needle").geometry)
