@@ -18,10 +18,12 @@
  *   - Geometry: circular cone beam, rotation axis z, volume centred at the
  *     origin; source S_j = DSO (cos t_j, sin t_j, 0); detector centre
  *     -(DSD - DSO)(cos t_j, sin t_j, 0); detector axes u = (-sin t_j, cos t_j, 0),
- *     v = (0, 0, 1); pixel (iu, iv) centre at (iu - (nu-1)/2) du along u and
- *     (iv - (nv-1)/2) dv along v; one ray per pixel from the source through
- *     the pixel centre.  The paper names only DSO, DSD and the pitch
- *     (Sec. 3.2); the rest is this library's convention.
+ *     v = (0, 0, 1); pixel (iu, iv) centre at (iu - (nu-1)/2) du + u_offset
+ *     along u and (iv - (nv-1)/2) dv along v; one ray per pixel from the
+ *     source through the pixel centre.  The paper names only DSO, DSD and the
+ *     pitch (Sec. 3.2); the rest is this library's convention.  The detector
+ *     may be shifted along u, not along v: the kernels pair every row with
+ *     its mirror about the plane z = 0 of the source.
  *   - A_ij = length in mm of ray i inside voxel j (exact ray/voxel-box
  *     intersection, i.e. Siddon weights).  A^T uses the same weights.
  *   - Volume layout: float32, index (ix*ny + iy)*nz + iz (z fastest).
@@ -105,6 +107,9 @@ typedef struct {
     int n_views;               /* >= 1 */
     const double *angles_rad;  /* host array of n_views angles; copied */
     int proj_layout;           /* PICCS_LAYOUT_UV or PICCS_LAYOUT_VU */
+    double u_offset;           /* detector shift along u, mm (finite; 0 = centred):
+                                  an offset detector, as on C-arms that widen the
+                                  field of view with a half-fan scan */
 } piccs_geometry;
 
 typedef struct {

@@ -33,7 +33,7 @@ class _Geom(C.Structure):
                 ("du", C.c_double), ("dv", C.c_double),
                 ("dso", C.c_double), ("dsd", C.c_double),
                 ("n_views", C.c_int), ("angles", C.POINTER(C.c_double)),
-                ("layout", C.c_int)]
+                ("layout", C.c_int), ("u_offset", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -87,7 +87,8 @@ class _GeomHandle:
     def __init__(self, g):
         self.angles = _f64(g.angles)
         self.s = _Geom(g.nx, g.ny, g.nz, g.vx, g.vy, g.vz, g.nu, g.nv, g.du, g.dv,
-                       g.dso, g.dsd, self.angles.shape[0], _pd(self.angles), g.layout)
+                       g.dso, g.dsd, self.angles.shape[0], _pd(self.angles), g.layout,
+                       float(getattr(g, "u_offset", 0.0)))
 
     @property
     def ref(self):

@@ -47,6 +47,8 @@ typedef struct {
     int n_views;
     const double *angles;
     int layout; /* 0: (j, iu, iv) v fastest; 1: (j, iv, iu) u fastest */
+    double u_offset; /* detector shift along u (mm): pixel centres at
+                        (iu - (nu-1)/2) du + u_offset */
 } og_geom;
 
 enum { OG_PICCS = 0, OG_PIPLE = 1, OG_TV = 2, OG_CGLS = 3 };
@@ -75,7 +77,7 @@ static void og_unpidx(const og_geom *g, long long r, int *j, int *iu, int *iv)
 static void og_ray(const og_geom *g, int j, int iu, int iv, double S[3], double P[3])
 {
     double c = cos(g->angles[j]), s = sin(g->angles[j]);
-    double u = (iu - (g->nu - 1) / 2.0) * g->du;
+    double u = (iu - (g->nu - 1) / 2.0) * g->du + g->u_offset;
     double v = (iv - (g->nv - 1) / 2.0) * g->dv;
     double back = g->dsd - g->dso;
     S[0] = g->dso * c; S[1] = g->dso * s; S[2] = 0.0;
@@ -360,8 +362,8 @@ void og_adjoint_voxels(const og_geom *g, const double *y, const long long *vox, 
                 if (vv < vmin) vmin = vv;
                 if (vv > vmax) vmax = vv;
             }
-            int iu0 = (int)floor(umin / g->du + (g->nu - 1) / 2.0) - 1;
-            int iu1 = (int)ceil(umax / g->du + (g->nu - 1) / 2.0) + 1;
+            int iu0 = (int)floor((umin - g->u_offset) / g->du + (g->nu - 1) / 2.0) - 1;
+            int iu1 = (int)ceil((umax - g->u_offset) / g->du + (g->nu - 1) / 2.0) + 1;
             int iv0 = (int)floor(vmin / g->dv + (g->nv - 1) / 2.0) - 1;
             int iv1 = (int)ceil(vmax / g->dv + (g->nv - 1) / 2.0) + 1;
             if (iu0 < 0) iu0 = 0;

@@ -51,7 +51,7 @@ class piccs_geometry(C.Structure):
                 ("du", C.c_double), ("dv", C.c_double),
                 ("dso", C.c_double), ("dsd", C.c_double),
                 ("n_views", C.c_int), ("angles_rad", C.POINTER(C.c_double)),
-                ("proj_layout", C.c_int)]
+                ("proj_layout", C.c_int), ("u_offset", C.c_double)]
 
 
 class piccs_params(C.Structure):
@@ -208,13 +208,14 @@ def _check(rc, ctx=None):
 
 def make_geometry(g):
     """piccs_geometry from any object with nx, ny, nz, vx, vy, vz, nu, nv, du,
-    dv, dso, dsd, angles (radians) and layout attributes.  The returned
-    structure keeps the angle array alive."""
+    dv, dso, dsd, angles (radians), layout and (optionally) u_offset
+    attributes.  The returned structure keeps the angle array alive."""
     ang = np.ascontiguousarray(np.asarray(g.angles, dtype=np.float64))
     s = piccs_geometry(int(g.nx), int(g.ny), int(g.nz), float(g.vx), float(g.vy), float(g.vz),
                        int(g.nu), int(g.nv), float(g.du), float(g.dv), float(g.dso),
                        float(g.dsd), int(ang.shape[0]),
-                       ang.ctypes.data_as(C.POINTER(C.c_double)), int(getattr(g, "layout", 0)))
+                       ang.ctypes.data_as(C.POINTER(C.c_double)), int(getattr(g, "layout", 0)),
+                       float(getattr(g, "u_offset", 0.0)))
     s._angles = ang
     return s
 

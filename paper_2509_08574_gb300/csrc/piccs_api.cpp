@@ -169,6 +169,7 @@ int check_geometry(const piccs_geometry *g, char *why, size_t n)
     // sizes below 1e-4 mm would push the FP32 crossing parameters out of range
     if (!finite_pos(g->vx) || !finite_pos(g->vy) || !finite_pos(g->vz) || g->vx < 1e-4 || g->vy < 1e-4 || g->vz < 1e-4) { snprintf(why, n, "voxel size must be finite and >= 1e-4 mm"); return PICCS_EINVAL; }
     if (!finite_pos(g->du) || !finite_pos(g->dv) || g->du < 1e-4 || g->dv < 1e-4) { snprintf(why, n, "detector pitch must be finite and >= 1e-4 mm"); return PICCS_EINVAL; }
+    if (!std::isfinite(g->u_offset)) { snprintf(why, n, "u_offset must be finite"); return PICCS_EINVAL; }
     if (!(g->dsd < 1e7)) { snprintf(why, n, "dsd must be below 1e7 mm"); return PICCS_EINVAL; }
     const double M = (double)g->nx * g->ny * g->nz;
     const double N = (double)g->n_views * g->nu * g->nv;

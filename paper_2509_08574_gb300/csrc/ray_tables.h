@@ -33,7 +33,7 @@ inline int walk_column(const piccs_geometry *g, int j, int iu, ColParams &cp, in
     const double cth = std::cos(g->angles_rad[j]), sth = std::sin(g->angles_rad[j]);
     const double Sx = g->dso * cth, Sy = g->dso * sth;
     const double back = g->dsd - g->dso;
-    const double u = (iu - 0.5 * (g->nu - 1)) * g->du;
+    const double u = (iu - 0.5 * (g->nu - 1)) * g->du + g->u_offset;
     const double Px = -back * cth - u * sth, Py = -back * sth + u * cth;
     const double dx = Px - Sx, dy = Py - Sy;
     const double D = std::sqrt(dx * dx + dy * dy);

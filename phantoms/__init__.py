@@ -16,7 +16,7 @@ is shared by the oracle and the CUDA path, each implementing it on its own):
 * view ``j`` at angle ``theta_j``: source ``S = DSO (cos, sin, 0)``, detector
   centre ``-(DSD - DSO)(cos, sin, 0)``, detector axes
   ``u = (-sin, cos, 0)`` and ``v = (0, 0, 1)``;
-* pixel ``(iu, iv)`` centre ``C + (iu - (nu-1)/2) du u + (iv - (nv-1)/2) dv v``;
+* pixel ``(iu, iv)`` centre ``C + ((iu - (nu-1)/2) du + u_offset) u + (iv - (nv-1)/2) dv v``;
   one ray per pixel, from the source through the pixel centre;
 * projection layout ``LAYOUT_UV``: ``(j*nu + iu)*nv + iv`` (v fastest, the
   native one) or ``LAYOUT_VU``: ``(j*nv + iv)*nu + iu`` (u fastest).
@@ -53,6 +53,7 @@ class Geometry:
     dsd: float
     angles: np.ndarray  # radians, float64, shape (n_views,)
     layout: int = LAYOUT_UV
+    u_offset: float = 0.0  # detector shift along u (mm)
 
     @property
     def n_views(self) -> int:
@@ -94,7 +95,7 @@ def ray_endpoints(g: Geometry, views: Optional[Sequence[int]] = None):
     src = np.stack([g.dso * c, g.dso * s, np.zeros_like(c)], axis=-1)
     det_c = np.stack([-(g.dsd - g.dso) * c, -(g.dsd - g.dso) * s, np.zeros_like(c)], axis=-1)
     uhat = np.stack([-s, c, np.zeros_like(c)], axis=-1)
-    u = (np.arange(g.nu) - (g.nu - 1) / 2.0) * g.du
+    u = (np.arange(g.nu) - (g.nu - 1) / 2.0) * g.du + g.u_offset
     v = (np.arange(g.nv) - (g.nv - 1) / 2.0) * g.dv
     if g.layout == LAYOUT_UV:
         uu, vv = np.meshgrid(u, v, indexing="ij")

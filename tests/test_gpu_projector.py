@@ -72,6 +72,13 @@ GEOMS = {
     # 3.75 rows per layer, some rays leaving through the top and bottom faces
     "prefix_dense_rows": lambda: P.Geometry(24, 22, 40, 1.0, 1.0, 1.0, 32, 96, 1.0, 0.4, 100.0,
                                             150.0, P.scan_angles(6, 360.0, 1.0)),
+    # offset detector (its centre 20 mm off the central ray, a half-fan scan):
+    # the even-size candidate gather
+    "offset_detector": lambda: P.Geometry(40, 36, 32, 1.0, 1.0, 1.0, 48, 40, 1.2, 1.0, 120.0, 200.0,
+                                          P.scan_angles(9, 360.0, 5.0), P.LAYOUT_UV, 20.0),
+    # offset the other way, 3.75 rows per layer: the prefix-sum gather
+    "offset_prefix": lambda: P.Geometry(24, 22, 40, 1.0, 1.0, 1.0, 32, 96, 1.0, 0.4, 100.0, 150.0,
+                                        P.scan_angles(6, 360.0, 1.0), P.LAYOUT_VU, -9.0),
     # truncated: detector smaller than the volume shadow, anisotropic voxels
     "truncated": lambda: P.Geometry(40, 36, 32, 0.8, 0.9, 0.6, 24, 40, 0.8, 0.5, 120.0, 180.0,
                                     P.scan_angles(9, 200.0, 5.0)),

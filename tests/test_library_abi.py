@@ -44,11 +44,19 @@ def test_every_declared_symbol_is_exported(pk):
 def test_validate_accepts_the_workloads(pk):
     for scan in (P.c1_small(), P.c2_needle(), P.c3_sphere_growth(), P.c5_carm()):
         pk.piccs_validate(scan.geometry, pk.make_params())
+    pk.piccs_validate(P.c1_small().geometry.replace(u_offset=-31.5), pk.make_params())
+
+
+def test_binding_geometry_carries_the_offset(pk):
+    g = P.c1_small().geometry.replace(u_offset=12.25)
+    s = pk.make_geometry(g)
+    assert s.u_offset == 12.25 and s.proj_layout == g.layout and s.n_views == g.n_views
 
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(nv=-1), dict(vx=0.0), dict(du=float("nan")), dict(dso=10.0),
     dict(dsd=1040.0), dict(layout=7), dict(angles=np.array([0.0, np.inf])),
+    dict(u_offset=float("inf")), dict(u_offset=float("nan")),
 ])
 def test_validate_rejects_bad_geometry(pk, bad):
     g = P.c1_small().geometry.replace(**bad)

@@ -84,9 +84,10 @@ def test_voxel_aligned_cube_is_exact():
     np.testing.assert_allclose(O.forward(g, x), exact, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("layout", [P.LAYOUT_UV, P.LAYOUT_VU])
-def test_matches_bruteforce_clipping_8cubed(layout):
-    g = P.tiny_geometry(layout=layout)
+@pytest.mark.parametrize("layout,u_offset", [(P.LAYOUT_UV, 0.0), (P.LAYOUT_VU, 0.0),
+                                             (P.LAYOUT_UV, 4.1), (P.LAYOUT_VU, -2.7)])
+def test_matches_bruteforce_clipping_8cubed(layout, u_offset):
+    g = P.tiny_geometry(layout=layout).replace(u_offset=u_offset)
     A_brute = _brute_dense_A(g)
     A_or = _dense_from_oracle(g)
     assert np.count_nonzero(A_brute > 1e-9) > 1000
@@ -114,8 +115,9 @@ def test_dot_product_identity_c1():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def test_adjoint_by_voxel_clipping_matches_walk():
-    g = P.tiny_geometry(n=(9, 8, 7), det=(14, 12), n_views=9, arc=200.0)
+@pytest.mark.parametrize("u_offset", [0.0, 6.3])
+def test_adjoint_by_voxel_clipping_matches_walk(u_offset):
+    g = P.tiny_geometry(n=(9, 8, 7), det=(14, 12), n_views=9, arc=200.0).replace(u_offset=u_offset)
     y = P.random_projections(g, 5)
     full = O.adjoint(g, y).reshape(-1)
     vox = np.arange(g.M)
@@ -185,3 +187,33 @@ def test_geometry_check_rejects_source_inside():
     assert not O.check(g.replace(dso=4.0))
     assert not O.check(g.replace(dsd=g.dso + 2.0))
     assert not O.check(g.replace(nz=0))
+
+
+def _columns(g, y, first, n):
+    """Detector columns first .. first+n-1 of projections y of geometry g."""
+    return y[:, first:first + n, :] if g.layout == P.LAYOUT_UV else y[:, :, first:first + n]
+
+
+@pytest.mark.parametrize("layout", [P.LAYOUT_UV, P.LAYOUT_VU])
+def test_offset_detector_is_a_window_of_a_wider_one(layout):
+    """A detector shifted by k pixels along u is columns 2k .. 2k+nu-1 of a
+    centred one 2k pixels wider (both put pixel iu at the same u): the oracle's
+    A and A^T and the analytic projection all see the offset as a relabelling
+    of the rays."""
+    k = 5
+    g = P.tiny_geometry(n=(9, 8, 7), det=(11, 10), n_views=5, arc=200.0, layout=layout)
+    off = g.replace(u_offset=k * g.du)
+    wide = g.replace(nu=g.nu + 2 * k)
+    x = P.random_volume(g, 6)
+    y_off = O.forward(off, x)
+    assert np.abs(y_off - O.forward(g, x)).max() > 0.1  # the shift changes the data
+    np.testing.assert_allclose(y_off, _columns(wide, O.forward(wide, x), 2 * k, g.nu),
+                               rtol=0, atol=1e-11)
+    ph = P.ellipsoid_phantom(g, 4, seed=9, body_mu=0.02)
+    np.testing.assert_allclose(P.project_analytic(ph, off),
+                               _columns(wide, P.project_analytic(ph, wide), 2 * k, g.nu),
+                               rtol=0, atol=1e-11)
+    r = P.random_projections(off, 7)
+    r_wide = np.zeros(wide.proj_shape())
+    _columns(wide, r_wide, 2 * k, g.nu)[...] = r
+    np.testing.assert_allclose(O.adjoint(off, r), O.adjoint(wide, r_wide), rtol=0, atol=1e-11)
